@@ -1,0 +1,377 @@
+/*
+ * Oracle (test infrastructure only): the packet loop, in FP64.
+ *
+ *   Sec. 3.1.1, Eq. init_freq : emission (x_i = 0 at line centre, Sec. 3.1.1
+ *                               allows it for optically thick media)
+ *   Sec. 3.1.2, Eq. lnR       : tau_event = -ln R, cell-by-cell walk, Eq. tauH
+ *   Sec. 3.1.3                : scattering (see scatter.c)
+ *   Sec. 3.2.4                : a tau_0 = a tau_cell + a tau_NL, Eq. atau0min
+ *   Sec. 6.1, Eq. SB          : next-event (peel-off) estimator, sum of
+ *                               W(theta) exp(-tau_esc), traced only while
+ *                               tau_esc <= tau_esc_max (50 in the paper)
+ *
+ * Readings taken here (the paper is silent on them):
+ *   - dust (absent from the paper) is grey with opacity k_d per cell; an
+ *     interaction is dust with probability k_d / (k_HI H + k_d); dust absorbs
+ *     with probability 1 - A, else scatters isotropically with the comoving
+ *     frequency unchanged;
+ *   - the emission event itself is peeled off with weight exp(-tau_esc);
+ *     dust scatterings peel off with W = 1;
+ *   - the peel-off weight is W(mu) = (1 + RQ mu^2) / (1 + RQ/3) (isotropic
+ *     scattering = 1), with the R/Q drawn for the actual scattering;
+ *   - the escape frequency is the lab-frame x_lab = x + k.u of the last cell,
+ *     reported either as x relative to the Doppler width at T_ref or as
+ *     Delta v = -x_lab v_th (red = positive Delta v);
+ *   - cameras are distant observers along coordinate axes; the image axes of
+ *     a camera along +/-e_a are (+/-e_{a+1}, e_{a+2}) (indices mod 3), the
+ *     image plane is centred on the box with half-width fov_half; peel-off
+ *     rays along a periodic axis have no observer and contribute nothing;
+ *   - spectral bins are half-open [lo, hi); escapes outside the range are
+ *     counted as under/overflow.
+ * RNG: event 0 is the emission (block 0: mu, phi, tau_event; block 1: source
+ * Gaussian); event e >= 1 is the e-th interaction, blocks as in scatter.c.
+ */
+#include "grid.h"
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+#include <unistd.h>
+
+#define O_PI 3.14159265358979323846
+#define O_MAX_TRIALS 1000000
+#define IMG_BUF 8192
+
+typedef struct {
+  const o_grid* g;
+  const o_params* p;
+  o_result* res;
+  uint32_t key[2];
+  double vth_ref;
+  int tid, nthreads;
+  pthread_mutex_t* img_lock;
+  /* private tallies */
+  uint64_t n_emitted, n_escaped, n_absorbed, n_capped, n_scat, n_scat_hi, n_cell, n_peel;
+  uint64_t under, over;
+  uint64_t* spec;
+  double* cam_spec;
+  double* cam_spec2;
+  double* cam_total;
+  int64_t img_n;
+  int64_t* img_idx;
+  double* img_w;
+} worker;
+
+static void draw_block(const uint32_t key[2], uint64_t pid, uint32_t event, uint32_t blk, double u[4]) {
+  uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), event, blk};
+  uint32_t r[4];
+  o_philox4x32_10(ctr, key, r);
+  for (int i = 0; i < 4; ++i) u[i] = o_uniform(r[i]);
+}
+
+static double dot3(const double p[3], const double q[3]) {
+  return p[0] * q[0] + p[1] * q[1] + p[2] * q[2];
+}
+
+static void flush_image(worker* w) {
+  if (w->img_n == 0) return;
+  pthread_mutex_lock(w->img_lock);
+  for (int64_t i = 0; i < w->img_n; ++i) w->res->cam_image[w->img_idx[i]] += w->img_w[i];
+  pthread_mutex_unlock(w->img_lock);
+  w->img_n = 0;
+}
+
+static int camera_axis(const double d[3], int* sgn) {
+  int a = 0;
+  if (fabs(d[1]) > fabs(d[a])) a = 1;
+  if (fabs(d[2]) > fabs(d[a])) a = 2;
+  *sgn = d[a] > 0.0 ? 1 : -1;
+  return a;
+}
+
+static double spectral_coord(int units, double x_lab, double vth, double vth_ref) {
+  return units == 0 ? x_lab * vth / vth_ref : -x_lab * vth;
+}
+
+static int bin_of(double s, double lo, double hi, int nb) {
+  if (!(s >= lo) || !(s < hi)) return -1;
+  int b = (int)floor((s - lo) * (double)nb / (hi - lo));
+  if (b < 0 || b >= nb) return -1;
+  return b;
+}
+
+/* Sec. 6.1: one peel-off ray from position r in cell c, comoving frequency
+ * x_c there, towards camera cam, with phase weight W. */
+static void peel(worker* w, int cam, const double r0[3], int64_t c0, double x_c, double W) {
+  const o_grid* g = w->g;
+  const o_params* p = w->p;
+  const double* k = p->cams[cam].dir;
+  int sgn;
+  int cax = camera_axis(k, &sgn);
+  if (g->periodic_xy && cax < 2) return;
+  double r[3] = {r0[0], r0[1], r0[2]};
+  int64_t c = c0;
+  double x = x_c;
+  double tau = 0.0;
+  for (;;) {
+    double clo[3], chi[3];
+    o_cell_bounds(g, c, clo, chi);
+    int ax;
+    double l = o_exit_distance(clo, chi, r, k, &ax);
+    double H = o_H_approx(g->a[c], x);
+    tau += (g->kHI[c] * H + g->kd[c]) * l;
+    w->n_peel++;
+    if (tau > p->tau_esc_max) return;
+    for (int i = 0; i < 3; ++i) r[i] += l * k[i];
+    int64_t nx = o_next_cell(g, c, ax, r, k);
+    if (nx < 0) break;
+    /* Sec. 3.1.2: frequency in the new cell's comoving frame */
+    x = (x + dot3(k, &g->u[3 * c])) * (g->vth[c] / g->vth[nx]) - dot3(k, &g->u[3 * nx]);
+    c = nx;
+  }
+  double x_lab = x + dot3(k, &g->u[3 * c]);
+  double s = spectral_coord(p->cam_units, x_lab, g->vth[c], w->vth_ref);
+  double wt = W * exp(-tau);
+  if (w->cam_total) w->cam_total[cam] += wt;
+  int b = bin_of(s, p->cam_lo, p->cam_hi, p->cam_nbins);
+  if (b < 0) return;
+  if (w->cam_spec) w->cam_spec[(size_t)cam * p->cam_nbins + b] += wt;
+  if (w->cam_spec2) w->cam_spec2[(size_t)cam * p->cam_nbins + b] += wt * wt;
+  int npix = p->cams[cam].npix;
+  if (npix > 0 && w->res->cam_image) {
+    /* image plane axes of this camera */
+    int au = (cax + 1) % 3, av = (cax + 2) % 3;
+    double cu = 0.5 * (g->lo[au] + g->hi[au]), cv = 0.5 * (g->lo[av] + g->hi[av]);
+    double pu = sgn * (r0[au] - cu), pv = r0[av] - cv;
+    double fu = (pu + p->fov_half) / (2.0 * p->fov_half) * npix;
+    double fv = (pv + p->fov_half) / (2.0 * p->fov_half) * npix;
+    if (fu >= 0.0 && fu < npix && fv >= 0.0 && fv < npix) {
+      int64_t iu = (int64_t)floor(fu), iv = (int64_t)floor(fv);
+      /* offset of this camera's cube within the image buffer */
+      int64_t off = 0;
+      for (int q = 0; q < cam; ++q) off += (int64_t)p->cams[q].npix * p->cams[q].npix * p->cam_nbins;
+      int64_t idx = off + ((iv * npix + iu) * p->cam_nbins) + b;
+      w->img_idx[w->img_n] = idx;
+      w->img_w[w->img_n] = wt;
+      if (++w->img_n == IMG_BUF) flush_image(w);
+    }
+  }
+}
+
+static void peel_all_hi(worker* w, const double r[3], int64_t c, double x, const double ki[3],
+                        const double u_atom[3], double g, double RQ) {
+  for (int cam = 0; cam < w->p->n_cam; ++cam) {
+    const double* kc = w->p->cams[cam].dir;
+    double mu_c = dot3(ki, kc);
+    double W = (1.0 + RQ * mu_c * mu_c) / (1.0 + RQ / 3.0);
+    double dk[3] = {kc[0] - ki[0], kc[1] - ki[1], kc[2] - ki[2]};
+    double x_c = x + dot3(dk, u_atom) + g * (mu_c - 1.0);
+    peel(w, cam, r, c, x_c, W);
+  }
+}
+
+static void peel_all_iso(worker* w, const double r[3], int64_t c, double x) {
+  for (int cam = 0; cam < w->p->n_cam; ++cam) peel(w, cam, r, c, x, 1.0);
+}
+
+static void run_packet(worker* w, uint64_t pid) {
+  const o_grid* g = w->g;
+  const o_params* p = w->p;
+  double B0[4], B1[4];
+  w->n_emitted++;
+  /* emission, event 0 */
+  draw_block(w->key, pid, 0, 0, B0);
+  double mu = 2.0 * B0[0] - 1.0, phi = 2.0 * O_PI * B0[1];
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  double k[3] = {st * cos(phi), st * sin(phi), mu};
+  double tau = -log(B0[2]);
+  double r[3] = {p->src_pos[0], p->src_pos[1], p->src_pos[2]};
+  if (p->src_sigma > 0.0) {
+    draw_block(w->key, pid, 0, 1, B1);
+    double rho1 = sqrt(-2.0 * log(B1[0])), rho2 = sqrt(-2.0 * log(B1[2]));
+    r[0] += p->src_sigma * rho1 * cos(2.0 * O_PI * B1[1]);
+    r[1] += p->src_sigma * rho1 * sin(2.0 * O_PI * B1[1]);
+    r[2] += p->src_sigma * rho2 * cos(2.0 * O_PI * B1[3]);
+  }
+  double x = 0.0;
+  uint64_t nscat = 0;
+  int status = 0;
+  double s_esc = 0.0;
+  int64_t c = o_locate_cell(g, r, k);
+  if (c < 0) {
+    /* source outside the domain: leaves at once, at line centre */
+    status = 1;
+    s_esc = 0.0;
+  } else {
+    peel_all_iso(w, r, c, x);
+  }
+  uint32_t event = 0;
+  while (status == 0) {
+    /* Sec. 3.1.2: march until tau_event is spent or the packet leaves */
+    int interact = 0;
+    for (;;) {
+      double clo[3], chi[3];
+      o_cell_bounds(g, c, clo, chi);
+      int ax;
+      double l = o_exit_distance(clo, chi, r, k, &ax);
+      double ktot = g->kHI[c] * o_H_approx(g->a[c], x) + g->kd[c];
+      double tau_cell = ktot * l;
+      w->n_cell++;
+      if (tau <= tau_cell) {
+        double le = tau / ktot;
+        for (int i = 0; i < 3; ++i) r[i] += le * k[i];
+        interact = 1;
+        break;
+      }
+      tau -= tau_cell;
+      for (int i = 0; i < 3; ++i) r[i] += l * k[i];
+      int64_t nx = o_next_cell(g, c, ax, r, k);
+      if (nx < 0) break;
+      x = (x + dot3(k, &g->u[3 * c])) * (g->vth[c] / g->vth[nx]) - dot3(k, &g->u[3 * nx]);
+      c = nx;
+    }
+    if (!interact) {
+      double x_lab = x + dot3(k, &g->u[3 * c]);
+      s_esc = spectral_coord(p->spec_units, x_lab, g->vth[c], w->vth_ref);
+      status = 1;
+      break;
+    }
+    /* interaction, event e */
+    ++event;
+    draw_block(w->key, pid, event, 0, B0);
+    double H = o_H_approx(g->a[c], x);
+    double ktot = g->kHI[c] * H + g->kd[c];
+    if (B0[0] * ktot < g->kd[c]) {
+      /* dust */
+      if (B0[1] >= p->albedo) { status = 2; break; }
+      draw_block(w->key, pid, event, 1, B1);
+      double m = 2.0 * B1[2] - 1.0, f = 2.0 * O_PI * B1[3];
+      double sm = sqrt(fmax(0.0, 1.0 - m * m));
+      k[0] = sm * cos(f); k[1] = sm * sin(f); k[2] = m;
+      nscat++;
+      peel_all_iso(w, r, c, x);
+    } else {
+      o_scatter_io s;
+      memset(&s, 0, sizeof(s));
+      s.x = x;
+      for (int i = 0; i < 3; ++i) s.k[i] = k[i];
+      s.a = g->a[c];
+      s.g = p->recoil ? g->g[c] : 0.0;
+      s.atau0 = p->core_skip ? g->a[c] * g->kHI[c] * o_min_face_distance(g, c, r) + g->atau_nl[c] : -1.0;
+      s.phase = p->phase;
+      s.pid = pid;
+      s.event = event;
+      o_scatter_hi(&s, w->key);
+      if (s.n_trials > O_MAX_TRIALS) { status = 3; break; }
+      nscat++;
+      w->n_scat_hi++;
+      peel_all_hi(w, r, c, x, k, s.u_atom, s.g, s.RQ);
+      for (int i = 0; i < 3; ++i) k[i] = s.k_f[i];
+      x = s.x_f;
+    }
+    if (nscat >= p->max_scatter) { status = 3; break; }
+    tau = -log(B0[2]);
+  }
+  w->n_scat += nscat;
+  if (status == 1) {
+    w->n_escaped++;
+    int b = bin_of(s_esc, p->spec_lo, p->spec_hi, p->spec_nbins);
+    if (b >= 0) w->spec[b]++;
+    else if (s_esc < p->spec_lo) w->under++;
+    else w->over++;
+  } else if (status == 2) {
+    w->n_absorbed++;
+  } else {
+    w->n_capped++;
+  }
+  if (p->pk_status) p->pk_status[pid] = status;
+  if (p->pk_nscat) p->pk_nscat[pid] = nscat;
+  if (p->pk_freq) p->pk_freq[pid] = (status == 1) ? s_esc : 0.0;
+}
+
+#define CHUNK 16
+
+static void* worker_main(void* arg) {
+  worker* w = (worker*)arg;
+  uint64_t n = w->p->n_packets;
+  for (uint64_t ch = (uint64_t)w->tid; ch * CHUNK < n; ch += (uint64_t)w->nthreads) {
+    uint64_t end = (ch + 1) * CHUNK;
+    if (end > n) end = n;
+    for (uint64_t pid = ch * CHUNK; pid < end; ++pid) run_packet(w, pid);
+  }
+  flush_image(w);
+  return NULL;
+}
+
+int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
+  struct timespec t0, t1;
+  clock_gettime(CLOCK_MONOTONIC, &t0);
+  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo) || !res->spec) return -1;
+  if (p->n_cam < 0 || (p->n_cam > 0 && (!p->cams || p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)))) return -1;
+  o_grid g;
+  int rc = o_grid_build(gin, &g);
+  if (rc) return rc;
+  if (p->core_skip) o_atau_nl_grid(&g, p->f_nl);
+  int nt = p->n_threads;
+  if (nt <= 0) nt = (int)sysconf(_SC_NPROCESSORS_ONLN);
+  if (nt < 1) nt = 1;
+  pthread_mutex_t lock;
+  pthread_mutex_init(&lock, NULL);
+  worker* ws = (worker*)calloc((size_t)nt, sizeof(worker));
+  pthread_t* th = (pthread_t*)calloc((size_t)nt, sizeof(pthread_t));
+  size_t ncs = (size_t)(p->n_cam > 0 ? p->n_cam : 0) * (size_t)(p->cam_nbins > 0 ? p->cam_nbins : 0);
+  for (int t = 0; t < nt; ++t) {
+    worker* w = &ws[t];
+    w->g = &g; w->p = p; w->res = res;
+    w->key[0] = (uint32_t)p->seed; w->key[1] = (uint32_t)(p->seed >> 32);
+    w->vth_ref = o_vth_kms(p->T_ref > 0.0 ? p->T_ref : 1.0e4);
+    w->tid = t; w->nthreads = nt; w->img_lock = &lock;
+    w->spec = (uint64_t*)calloc((size_t)p->spec_nbins, sizeof(uint64_t));
+    if (ncs) {
+      w->cam_spec = (double*)calloc(ncs, sizeof(double));
+      w->cam_spec2 = (double*)calloc(ncs, sizeof(double));
+      w->cam_total = (double*)calloc((size_t)p->n_cam, sizeof(double));
+    }
+    w->img_idx = (int64_t*)malloc(IMG_BUF * sizeof(int64_t));
+    w->img_w = (double*)malloc(IMG_BUF * sizeof(double));
+  }
+  if (res->cam_image) {
+    size_t nimg = 0;
+    for (int q = 0; q < p->n_cam; ++q) nimg += (size_t)p->cams[q].npix * p->cams[q].npix * p->cam_nbins;
+    memset(res->cam_image, 0, nimg * sizeof(double));
+  }
+  for (int t = 0; t < nt; ++t) pthread_create(&th[t], NULL, worker_main, &ws[t]);
+  for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+  /* merge in thread order */
+  memset(res->spec, 0, (size_t)p->spec_nbins * sizeof(uint64_t));
+  res->n_emitted = res->n_escaped = res->n_absorbed = res->n_capped = 0;
+  res->n_scat = res->n_scat_hi = res->n_cell_visits = res->n_peel_visits = 0;
+  res->spec_under = res->spec_over = 0;
+  if (res->cam_spec) memset(res->cam_spec, 0, ncs * sizeof(double));
+  if (res->cam_spec2) memset(res->cam_spec2, 0, ncs * sizeof(double));
+  if (res->cam_total) memset(res->cam_total, 0, (size_t)p->n_cam * sizeof(double));
+  for (int t = 0; t < nt; ++t) {
+    worker* w = &ws[t];
+    res->n_emitted += w->n_emitted; res->n_escaped += w->n_escaped;
+    res->n_absorbed += w->n_absorbed; res->n_capped += w->n_capped;
+    res->n_scat += w->n_scat; res->n_scat_hi += w->n_scat_hi;
+    res->n_cell_visits += w->n_cell; res->n_peel_visits += w->n_peel;
+    res->spec_under += w->under; res->spec_over += w->over;
+    for (int b = 0; b < p->spec_nbins; ++b) res->spec[b] += w->spec[b];
+    for (size_t i = 0; i < ncs; ++i) {
+      if (res->cam_spec) res->cam_spec[i] += w->cam_spec[i];
+      if (res->cam_spec2) res->cam_spec2[i] += w->cam_spec2[i];
+    }
+    if (res->cam_total) for (int q = 0; q < p->n_cam; ++q) res->cam_total[q] += w->cam_total[q];
+    free(w->spec); free(w->cam_spec); free(w->cam_spec2); free(w->cam_total);
+    free(w->img_idx); free(w->img_w);
+  }
+  free(ws); free(th);
+  pthread_mutex_destroy(&lock);
+  o_grid_free(&g);
+  clock_gettime(CLOCK_MONOTONIC, &t1);
+  res->n_threads_used = nt;
+  res->seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+  return 0;
+}
