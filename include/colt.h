@@ -1,0 +1,250 @@
+/*
+ * libcolt -- GB300 (sm_103a) Lyman-alpha Monte-Carlo radiative transfer.
+ *
+ * The packet transport loop of Smith, Safranek-Shrader, Bromm & Milosavljevic
+ * (2014), "The Lyman-alpha signature of the first galaxies" (COLT): emission
+ * (Sec. 3.1.1), optical-depth draws and the cell-by-cell march (Sec. 3.1.2,
+ * Eq. lnR, Eq. tauH), resonant scattering with the u_par rejection sampler,
+ * core-skipping, dipole phase function and recoil (Sec. 3.1.3, 3.2.1-3.2.4),
+ * grey dust, and next-event (peel-off) camera tallies (Sec. 6.1, Eq. SB).
+ *
+ * Conventions for every call:
+ *   - Return value: COLT_OK (0) or a negative colt_status.  No exception or
+ *     abort crosses this boundary.  colt_last_error() gives a message.
+ *   - Host pointers are read/written synchronously unless stated otherwise;
+ *     device pointers are read on the context's stream.
+ *   - The library owns every device buffer it allocates; callers keep
+ *     ownership of everything they pass in.
+ *   - One context per process and device.  All calls on a context are
+ *     serialised by an internal mutex.
+ *   - Units: lengths in cm, velocities in km/s, temperatures in K, densities
+ *     in cm^-3, dust opacity in cm^-1.  Frequencies are the paper's
+ *     x = (nu - nu_0) / Delta nu_D (Sec. 2) or Doppler velocity
+ *     Delta v = -x v_th in km/s (red = positive).
+ */
+#ifndef COLT_H
+#define COLT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct colt_ctx colt_ctx;
+typedef uint64_t colt_grid;   /* grid handle, 0 is never valid    */
+typedef uint64_t colt_req;    /* request handle, 0 is never valid */
+
+typedef enum {
+  COLT_OK = 0,
+  COLT_EINVAL = -1,     /* bad argument                                   */
+  COLT_ENOMEM = -2,     /* would exceed the memory budget / allocation    */
+  COLT_EAGAIN = -3,     /* not admitted yet (serving); retry later        */
+  COLT_ETIMEOUT = -4,   /* a bounded wait ran out                         */
+  COLT_ECUDA = -5,      /* a CUDA runtime call failed                     */
+  COLT_ENOTFOUND = -6,  /* unknown handle                                 */
+  COLT_EDEVICE = -7     /* a kernel raised its device-side error flag     */
+} colt_status;
+
+enum { COLT_CARTESIAN = 0, COLT_OCTREE = 1 };
+enum { COLT_MEM_HOST = 0, COLT_MEM_DEVICE = 1 };
+enum { COLT_PLAIN = 0, COLT_MIXED = 1 };          /* arithmetic of the transport */
+enum { COLT_PHASE_DIPOLE = 0, COLT_PHASE_ISOTROPIC = 1 };
+enum { COLT_UNITS_X = 0, COLT_UNITS_DV_KMS = 1 };
+
+/* ------------------------------------------------------------- context -- */
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds what the
+ * serving admission may hold resident (0 = 90% of free device memory).
+ * cuda_stream (a cudaStream_t, may be NULL) is the stream all work runs on;
+ * NULL makes the library create its own non-blocking stream.
+ * Fails with COLT_ECUDA when no usable device exists. */
+int colt_init(colt_ctx** ctx, int device, size_t mem_budget_bytes, void* cuda_stream);
+void colt_finalize(colt_ctx* ctx);
+const char* colt_last_error(colt_ctx* ctx);
+/* SM count, L2 bytes and library build info (for reports). */
+int colt_device_info(colt_ctx* ctx, int* sm_count, size_t* l2_bytes, int* cc_major, int* cc_minor);
+
+/* ---------------------------------------------------------------- grids -- */
+/* Per-cell inputs as the paper reads them (Sec. 3, first paragraph): density,
+ * temperature and bulk velocity per cell, plus grey dust opacity.
+ *   Cartesian: nx*ny*nz cells, x fastest, spanning the box [lo, hi).
+ *   Octree: n_cells leaves; leaf i has refinement level leaf_level[i] (0 =
+ *   root) and integer coordinates leaf_ijk[3i..3i+2] at that level, i.e. it
+ *   spans lo + ijk (hi-lo) 2^-level .. lo + (ijk+1) (hi-lo) 2^-level.  The
+ *   leaves must tile the box exactly (checked: COLT_EINVAL otherwise).
+ *   leaf_level / leaf_ijk are host arrays.
+ * Field arrays (n_cells FP32 each) are host or device memory per fields_mem;
+ * k_dust may be NULL (no dust).  T must be > 0 everywhere (empty cells carry
+ * any positive temperature).
+ * periodic_xy (Cartesian only): the box wraps in x and y (infinite slab).
+ * f_nl: threshold of the non-local a*tau estimate (Sec. 3.2.4, Eq. atauNL),
+ * computed once here on the device for every cell; 0 disables it.
+ * The library copies the fields into its own packed device records. */
+typedef struct {
+  int kind;
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  int periodic_xy;
+  int64_t n_cells;
+  const uint8_t* leaf_level;
+  const uint32_t* leaf_ijk;
+  const float* n_HI;
+  const float* T;
+  const float* vx;
+  const float* vy;
+  const float* vz;
+  const float* k_dust;
+  int fields_mem;
+  double f_nl;
+} colt_grid_desc;
+
+int colt_create_grid(colt_ctx* ctx, const colt_grid_desc* desc, colt_grid* out);
+int colt_destroy_grid(colt_ctx* ctx, colt_grid grid);
+/* Copy the packed per-cell records back to the host: 8 floats per cell,
+ * (k_HI = n_HI sigma_0 [cm^-1], a, k_dust [cm^-1], 1/v_th [s/km],
+ *  u_x, u_y, u_z [v/v_th], a tau_NL).  n_floats must be 8 * n_cells. */
+int colt_read_cells(colt_ctx* ctx, colt_grid grid, float* out, size_t n_floats);
+
+/* ------------------------------------------------------------------ runs -- */
+/* A distant observer along a coordinate axis (Sec. 6.1: six axis cameras).
+ * dir must be +-e_x, +-e_y or +-e_z.  The image axes of a camera along +-e_a
+ * are (+-e_{a+1}, e_{a+2}) (indices mod 3); npix = 0 gives a spectrum only. */
+typedef struct {
+  double dir[3];
+  int npix;
+} colt_camera;
+
+typedef struct {
+  uint64_t n_packets;
+  uint64_t seed;            /* Philox key; results depend only on (seed, packet id) */
+  double src_pos[3];        /* point source position (cm)                            */
+  double src_sigma;         /* Gaussian spread of the source (cm), 0 = point          */
+  int core_skip;            /* Sec. 3.2.4                                             */
+  int recoil;               /* Eq. recoil                                             */
+  int phase;                /* COLT_PHASE_DIPOLE (Eq. phaseW) or _ISOTROPIC           */
+  double tau_esc_max;       /* peel-off cutoff, 50 in Sec. 6.1                        */
+  double albedo;            /* dust albedo A                                          */
+  uint64_t max_scatter;     /* per-packet cap on scatterings (0 = none)               */
+  /* angle-averaged escape spectrum: bins [lo, hi) in spec_units */
+  int spec_units;           /* COLT_UNITS_X (x at T_ref) or COLT_UNITS_DV_KMS         */
+  double T_ref;
+  double spec_lo, spec_hi;
+  int spec_nbins;
+  /* peel-off cameras */
+  int n_cam;
+  const colt_camera* cams;  /* host array of n_cam                                    */
+  int cam_units;
+  double cam_lo, cam_hi;
+  int cam_nbins;
+  double fov_half;          /* image half-width (cm) about the box centre; 0 = box    */
+  int precision;            /* COLT_PLAIN (FP64 arithmetic) or COLT_MIXED             */
+  int block_size;           /* 0 = library default (autotuned)                        */
+  int blocks_per_sm;        /* 0 = library default                                    */
+  uint64_t pid_offset;      /* packets are ids pid_offset .. pid_offset + n_packets-1
+                               (random streams are keyed by id, so a job split into
+                               id ranges -- batches, replicas -- sums to the same
+                               tallies); per-packet outputs are indexed from 0      */
+} colt_run_params;
+
+/* Outputs of a run.  Counters are always filled; every array pointer may be
+ * NULL (not wanted).  Arrays are HOST memory of the stated lengths:
+ *   spec       [spec_nbins]                       escaped packets per bin
+ *   cam_spec   [n_cam * cam_nbins]                sum of W exp(-tau_esc) (Eq. SB)
+ *   cam_spec2  [n_cam * cam_nbins]                sum of squared weights
+ *   cam_image  [sum_c npix_c^2 * cam_nbins]       per camera [v][u][bin]
+ *   pk_status  [n_packets] 1 escaped, 2 absorbed, 3 capped
+ *   pk_nscat   [n_packets] executed scatterings of each packet
+ *   pk_freq    [n_packets] escape frequency (spec_units) of escaped packets */
+typedef struct {
+  uint64_t n_emitted, n_escaped, n_absorbed, n_capped;
+  uint64_t n_scat, n_scat_hi;
+  uint64_t n_cell_visits, n_peel_visits, n_peel_rays;
+  uint64_t spec_under, spec_over;
+  double kernel_ms;         /* device time of the transport kernel (CUDA events) */
+  uint64_t* spec;
+  double* cam_spec;
+  double* cam_spec2;
+  double* cam_image;
+  int32_t* pk_status;
+  uint64_t* pk_nscat;
+  double* pk_freq;
+} colt_result;
+
+/* Blocking solve: all packets of p on grid.  Results as above.
+ * COLT_EDEVICE if the kernel's bounds checks fired (results then invalid). */
+int colt_run(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_result* out);
+
+/* Blocking batched solve: n (1..256) independent solves -- each with its own
+ * grid, parameters and results (arrays of n) -- share one persistent launch,
+ * so short and long solves fill the GPU together.  params[i].precision must
+ * be equal for all i.  out[i].kernel_ms is the shared launch's time. */
+int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
+                   colt_result* out);
+
+/* Same solve with HOST input fields: builds a temporary grid from desc, runs,
+ * copies results back and frees the grid (one call for an end-to-end user). */
+int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params* p, colt_result* out);
+
+/* ------------------------------------------------------------- serving -- */
+/* Continuous batching.  colt_submit enqueues a solve (non-blocking); requests
+ * are admitted as memory (mem_budget_bytes) and batch slots free up, and the
+ * packets of all admitted requests share persistent launches.  Returns
+ * COLT_EAGAIN when the request cannot be queued now (queue full).  The grid
+ * must stay alive until the request is released.  Results of a request are
+ * identical to colt_run of the same (grid, params) up to floating-point
+ * summation order of the peel-off tallies. */
+typedef struct {
+  int done;                 /* 1 when all packets are finished                   */
+  int admitted;
+  uint64_t packets_done, packets_total;
+  double submit_to_done_ms; /* latency, valid when done                          */
+} colt_stats;
+
+int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);
+/* Drives the scheduler one step if work is pending and reports the request's
+ * state; never blocks longer than one batched launch. */
+int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st);
+/* Block until req is done or timeout_ms elapses (COLT_ETIMEOUT). */
+int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms);
+/* camera = -1: the angle-averaged escape spectrum (as doubles); else the
+ * camera's peel-off spectrum.  nbins must match the request's bin count. */
+int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t nbins);
+int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out);
+int colt_release(colt_ctx* ctx, colt_req req);
+
+/* ------------------------------------------------------ parity helpers -- */
+/* App. A1, Eq. AB: H_approx(a, x) for n pairs.  mem says where a, x, H live.
+ * precision COLT_MIXED evaluates in FP32 on float arrays; COLT_PLAIN in FP64
+ * on double arrays. */
+int colt_voigt(colt_ctx* ctx, const void* a, const void* x, void* H, size_t n, int precision, int mem);
+
+/* One resonant scattering per element (Sec. 3.1.3, 3.2.3, 3.2.4), with the
+ * transport kernel's own device code and RNG layout:
+ * Philox4x32-10 key (seed lo, seed hi), counter (pid lo, pid hi, event, block).
+ * Inputs and outputs are in FP64 here; the arithmetic is the precision's. */
+typedef struct {
+  double x;          /* incoming comoving frequency                            */
+  double k[3];       /* incoming direction                                     */
+  double a;          /* damping parameter                                      */
+  double g;          /* recoil parameter (0 = off)                             */
+  double atau0;      /* a tau_0 for x_crit (Eq. xcrit); < 0: core-skipping off */
+  int32_t phase;     /* COLT_PHASE_*                                           */
+  uint64_t pid;
+  uint32_t event;
+  double x_f;        /* outputs                                                */
+  double k_f[3];
+  double u_atom[3];
+  double u_par;
+  double x_crit;
+  double RQ;
+  double mu;
+  int32_t n_trials;
+} colt_scatter_io;
+
+int colt_scatter(colt_ctx* ctx, colt_scatter_io* io, size_t n, uint64_t seed, int precision);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

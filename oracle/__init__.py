@@ -47,7 +47,8 @@ class Params(C.Structure):
                 ("spec_nbins", C.c_int), ("n_cam", C.c_int), ("cams", C.c_void_p),
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double),
                 ("cam_nbins", C.c_int), ("fov_half", C.c_double), ("n_threads", C.c_int),
-                ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p)]
+                ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p),
+                ("pid0", C.c_uint64)]
 
 
 class Result(C.Structure):
@@ -226,10 +227,12 @@ def octree_locate(g, pos, direction):
     return int(lib().o_octree_locate(C.byref(s), _ptr(p), _ptr(d)))
 
 
-def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False) -> dict:
-    """Full packet loop on grid g with run description spec (synth.RunSpec)."""
+def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False, pid0: int = 0) -> dict:
+    """Full packet loop on grid g with run description spec (synth.RunSpec);
+    packets are ids pid0 .. pid0 + spec.n_packets - 1."""
     s, keep = _grid_struct(g)
     p = Params()
+    p.pid0 = int(pid0) + int(getattr(spec, "pid_offset", 0) or 0)
     p.n_packets = int(spec.n_packets)
     p.seed = int(spec.seed)
     p.src_pos = (C.c_double * 3)(*[float(v) for v in spec.src_pos])

@@ -28,6 +28,8 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <pthread.h>
+#include <unistd.h>
 
 static void free_all(o_grid* g) {
   free(g->kHI); free(g->a); free(g->vth); free(g->u); free(g->kd); free(g->g);
@@ -268,10 +270,9 @@ double o_min_face_distance(const o_grid* g, int64_t c, const double r[3]) {
   return m < 0.0 ? 0.0 : m;
 }
 
-/* Eq. atauNL. */
-int o_atau_nl_grid(o_grid* g, double f_nl) {
-  int64_t n = g->n_cells;
-  for (int64_t c = 0; c < n; ++c) {
+/* Eq. atauNL for cells [c0, c1). */
+static void atau_nl_range(o_grid* g, double f_nl, int64_t c0, int64_t c1) {
+  for (int64_t c = c0; c < c1; ++c) {
     double nref = g->nHI[c];
     if (!(nref > 0.0) || !(f_nl > 0.0)) { g->atau_nl[c] = 0.0; continue; }
     double clo[3], chi[3];
@@ -302,6 +303,33 @@ int o_atau_nl_grid(o_grid* g, double f_nl) {
     }
     g->atau_nl[c] = best;
   }
+}
+
+typedef struct { o_grid* g; double f_nl; int64_t c0, c1; } nl_job;
+
+static void* nl_worker(void* arg) {
+  nl_job* j = (nl_job*)arg;
+  atau_nl_range(j->g, j->f_nl, j->c0, j->c1);
+  return NULL;
+}
+
+/* Eq. atauNL: cells are independent, so they are split across host threads. */
+int o_atau_nl_grid(o_grid* g, double f_nl) {
+  int nt = (int)sysconf(_SC_NPROCESSORS_ONLN);
+  if (nt < 1) nt = 1;
+  if (nt > 64) nt = 64;
+  if (g->n_cells < 4096) nt = 1;
+  pthread_t th[64];
+  nl_job jobs[64];
+  int64_t per = (g->n_cells + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    jobs[t].g = g; jobs[t].f_nl = f_nl;
+    jobs[t].c0 = t * per;
+    jobs[t].c1 = (t + 1) * per < g->n_cells ? (t + 1) * per : g->n_cells;
+    if (jobs[t].c0 > jobs[t].c1) jobs[t].c0 = jobs[t].c1;
+    pthread_create(&th[t], NULL, nl_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
   return 0;
 }
 

@@ -132,6 +132,7 @@ typedef struct {
   int32_t*  pk_status;      /* 1 escaped, 2 absorbed, 3 capped                 */
   uint64_t* pk_nscat;
   double*   pk_freq;        /* escape spectral coordinate (escaped only)       */
+  uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
 } o_params;
 
 typedef struct {

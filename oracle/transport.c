@@ -27,7 +27,9 @@
  *     image plane is centred on the box with half-width fov_half; peel-off
  *     rays along a periodic axis have no observer and contribute nothing;
  *   - spectral bins are half-open [lo, hi); escapes outside the range are
- *     counted as under/overflow.
+ *     counted as under/overflow;
+ *   - a flight that visits more than 2^24 cells (only possible on periodic
+ *     grids with empty cells) ends the packet as capped.
  * RNG: event 0 is the emission (block 0: mu, phi, tau_event; block 1: source
  * Gaussian); event e >= 1 is the e-th interaction, blocks as in scatter.c.
  */
@@ -42,6 +44,9 @@
 #define O_PI 3.14159265358979323846
 #define O_MAX_TRIALS 1000000
 #define IMG_BUF 8192
+/* A flight visiting more cells than this (possible only on periodic grids
+ * with empty cells) ends the packet as capped. */
+#define O_MAX_FLIGHT_VISITS (1u << 24)
 
 typedef struct {
   const o_grid* g;
@@ -175,7 +180,8 @@ static void peel_all_iso(worker* w, const double r[3], int64_t c, double x) {
   for (int cam = 0; cam < w->p->n_cam; ++cam) peel(w, cam, r, c, x, 1.0);
 }
 
-static void run_packet(worker* w, uint64_t pid) {
+static void run_packet(worker* w, uint64_t idx) {
+  const uint64_t pid = w->p->pid0 + idx;
   const o_grid* g = w->g;
   const o_params* p = w->p;
   double B0[4], B1[4];
@@ -210,7 +216,9 @@ static void run_packet(worker* w, uint64_t pid) {
   while (status == 0) {
     /* Sec. 3.1.2: march until tau_event is spent or the packet leaves */
     int interact = 0;
+    uint32_t visits = 0;
     for (;;) {
+      if (++visits > O_MAX_FLIGHT_VISITS) { status = 3; break; }
       double clo[3], chi[3];
       o_cell_bounds(g, c, clo, chi);
       int ax;
@@ -231,6 +239,7 @@ static void run_packet(worker* w, uint64_t pid) {
       x = (x + dot3(k, &g->u[3 * c])) * (g->vth[c] / g->vth[nx]) - dot3(k, &g->u[3 * nx]);
       c = nx;
     }
+    if (status == 3) break;
     if (!interact) {
       double x_lab = x + dot3(k, &g->u[3 * c]);
       s_esc = spectral_coord(p->spec_units, x_lab, g->vth[c], w->vth_ref);
@@ -285,9 +294,9 @@ static void run_packet(worker* w, uint64_t pid) {
   } else {
     w->n_capped++;
   }
-  if (p->pk_status) p->pk_status[pid] = status;
-  if (p->pk_nscat) p->pk_nscat[pid] = nscat;
-  if (p->pk_freq) p->pk_freq[pid] = (status == 1) ? s_esc : 0.0;
+  if (p->pk_status) p->pk_status[idx] = status;
+  if (p->pk_nscat) p->pk_nscat[idx] = nscat;
+  if (p->pk_freq) p->pk_freq[idx] = (status == 1) ? s_esc : 0.0;
 }
 
 #define CHUNK 16

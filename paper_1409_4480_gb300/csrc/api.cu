@@ -1,0 +1,923 @@
+// C ABI of libcolt (declared and documented in include/colt.h): contexts,
+// grids, blocking runs, the continuous-batching scheduler and the parity
+// helpers.  Host-side runtime in C++17; all compute is in the CUDA kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "colt.h"
+#include "internal.h"
+
+using namespace colt;
+
+namespace {
+
+constexpr int kMaxJobs = 256;            // requests per persistent launch
+constexpr uint64_t kStepPackets = 1ull << 18;  // packet budget of one serving step
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct GridObj {
+  GridDev dev;
+  float4* rec = nullptr;
+  size_t bytes = 0;
+};
+
+struct Req;
+
+// Device + pinned staging for one persistent launch: header, job_end, jobs.
+struct LaunchBuf {
+  unsigned char* host = nullptr;        // pinned
+  unsigned char* dev = nullptr;
+  size_t bytes = 0;
+  unsigned long long* work = nullptr;   // device: next counter + launch counters
+  int* error = nullptr;
+  LaunchDev* hdr_h() { return reinterpret_cast<LaunchDev*>(host); }
+  unsigned long long* end_h() { return reinterpret_cast<unsigned long long*>(host + 256); }
+  Job* jobs_h() { return reinterpret_cast<Job*>(host + 256 + 8 * kMaxJobs); }
+  size_t off_end() const { return 256; }
+  size_t off_jobs() const { return 256 + 8 * kMaxJobs; }
+};
+
+struct Tally {
+  unsigned long long* spec = nullptr;
+  unsigned long long* counters = nullptr;
+  double* cam_spec = nullptr;
+  double* cam_spec2 = nullptr;
+  double* cam_image = nullptr;
+  int32_t* pk_status = nullptr;
+  uint64_t* pk_nscat = nullptr;
+  double* pk_freq = nullptr;
+  size_t bytes = 0;
+  void* block = nullptr;                // one allocation holds everything
+  cudaStream_t stream = nullptr;        // stream-ordered pool allocation
+};
+
+enum ReqState { kQueued = 0, kAdmitted = 1, kDone = 2 };
+
+struct Req {
+  uint64_t id = 0;
+  colt_grid grid = 0;
+  colt_run_params p{};
+  std::vector<colt_camera> cams;
+  RunDev run;                           // filled at admission (tally pointers)
+  Tally tally;
+  int state = kQueued;
+  uint64_t next_local = 0;              // packets handed to launches
+  uint64_t in_flight = 0;               // packets of the launch in flight
+  uint64_t done_packets = 0;
+  double t_submit = 0, t_done = 0;
+  size_t need_bytes = 0;
+};
+
+}  // namespace
+
+struct colt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t used = 0;
+  int sm_count = 0;
+  size_t l2 = 0;
+  int cc_major = 0, cc_minor = 0;
+  std::recursive_mutex mu;
+  std::string err;
+  uint64_t next_handle = 1;
+  std::map<uint64_t, GridObj> grids;
+  std::map<uint64_t, std::unique_ptr<Req>> reqs;
+  std::deque<uint64_t> queue;           // queued request ids (FIFO)
+  LaunchBuf lb;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_step = nullptr;
+  // serving
+  bool step_in_flight = false;
+  std::vector<std::pair<uint64_t, uint64_t>> step_jobs;  // (req id, packets)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int fail(colt_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(colt_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, COLT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// --- Sec. 2 line constants (T4 = T / 1e4 K) for the per-cell records ------
+inline double vth_kms(double T) { return 12.85 * std::sqrt(T / 1.0e4); }
+inline double damping_a(double T) { return 4.702e-4 / std::sqrt(T / 1.0e4); }
+inline double sigma0(double T) { return 5.898e-14 / std::sqrt(T / 1.0e4); }
+
+int camera_axis(const double d[3], int* axis, int* sgn) {
+  int nz = 0, ax = -1;
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] != 0.0) { ++nz; ax = a; }
+  }
+  if (nz != 1 || std::fabs(d[ax]) != 1.0) return -1;
+  *axis = ax;
+  *sgn = d[ax] > 0 ? 1 : -1;
+  return 0;
+}
+
+int validate_params(colt_ctx* ctx, const GridObj& g, const colt_run_params* p) {
+  if (!p) return fail(ctx, COLT_EINVAL, "params is NULL");
+  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo)) return fail(ctx, COLT_EINVAL, "bad escape-spectrum bins");
+  if (p->n_cam < 0 || p->n_cam > kMaxCams) return fail(ctx, COLT_EINVAL, "n_cam must be in [0, 8]");
+  if (p->n_cam > 0) {
+    if (!p->cams) return fail(ctx, COLT_EINVAL, "cams is NULL");
+    if (p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)) return fail(ctx, COLT_EINVAL, "bad camera bins");
+    for (int i = 0; i < p->n_cam; ++i) {
+      int ax, s;
+      if (camera_axis(p->cams[i].dir, &ax, &s)) return fail(ctx, COLT_EINVAL, "camera direction must be a coordinate axis");
+      if (p->cams[i].npix < 0 || p->cams[i].npix > 65536) return fail(ctx, COLT_EINVAL, "bad npix");
+    }
+  }
+  if (p->precision != COLT_PLAIN && p->precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
+  if (p->phase != COLT_PHASE_DIPOLE && p->phase != COLT_PHASE_ISOTROPIC) return fail(ctx, COLT_EINVAL, "bad phase");
+  if (p->spec_units != COLT_UNITS_X && p->spec_units != COLT_UNITS_DV_KMS) return fail(ctx, COLT_EINVAL, "bad spec_units");
+  if (p->n_cam > 0 && p->cam_units != COLT_UNITS_X && p->cam_units != COLT_UNITS_DV_KMS)
+    return fail(ctx, COLT_EINVAL, "bad cam_units");
+  if ((p->spec_units == COLT_UNITS_X || p->cam_units == COLT_UNITS_X) && !(p->T_ref > 0))
+    return fail(ctx, COLT_EINVAL, "T_ref must be > 0 for x units");
+  if (!(p->tau_esc_max > 0)) return fail(ctx, COLT_EINVAL, "tau_esc_max must be > 0");
+  if (!(p->albedo >= 0 && p->albedo <= 1)) return fail(ctx, COLT_EINVAL, "albedo must be in [0,1]");
+  if (!(p->src_sigma >= 0)) return fail(ctx, COLT_EINVAL, "src_sigma must be >= 0");
+  (void)g;
+  return COLT_OK;
+}
+
+size_t tally_bytes(const colt_run_params* p, bool per_packet) {
+  auto r = [](size_t n) { return (n + 255) & ~size_t(255); };
+  size_t b = 0;
+  b += r(sizeof(unsigned long long) * (size_t)p->spec_nbins);
+  b += r(sizeof(unsigned long long) * kNumCounters);
+  if (p->n_cam > 0) {
+    b += 2 * r(sizeof(double) * (size_t)p->n_cam * p->cam_nbins);
+    size_t img = 0;
+    for (int i = 0; i < p->n_cam; ++i) img += (size_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
+    if (img) b += r(sizeof(double) * img);
+  }
+  if (per_packet)
+    b += r(sizeof(int32_t) * p->n_packets) + r(sizeof(uint64_t) * p->n_packets) + r(sizeof(double) * p->n_packets);
+  return b;
+}
+
+// Allocate and zero one request's tallies on the context stream.
+int alloc_tally(colt_ctx* ctx, const colt_run_params* p, bool per_packet, Tally* t) {
+  t->bytes = tally_bytes(p, per_packet) + 256;
+  t->stream = ctx->stream;
+  CU(cudaMallocAsync(&t->block, t->bytes, ctx->stream));
+  CU(cudaMemsetAsync(t->block, 0, t->bytes, ctx->stream));
+  unsigned char* q = static_cast<unsigned char*>(t->block);
+  auto take = [&](size_t n) {
+    unsigned char* r = q;
+    q += (n + 255) & ~size_t(255);
+    return r;
+  };
+  t->counters = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * kNumCounters));
+  t->spec = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * p->spec_nbins));
+  if (p->n_cam > 0) {
+    t->cam_spec = reinterpret_cast<double*>(take(sizeof(double) * p->n_cam * p->cam_nbins));
+    t->cam_spec2 = reinterpret_cast<double*>(take(sizeof(double) * p->n_cam * p->cam_nbins));
+    size_t img = 0;
+    for (int i = 0; i < p->n_cam; ++i) img += (size_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
+    if (img) t->cam_image = reinterpret_cast<double*>(take(sizeof(double) * img));
+  }
+  if (per_packet) {
+    t->pk_status = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * p->n_packets));
+    t->pk_nscat = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * p->n_packets));
+    t->pk_freq = reinterpret_cast<double*>(take(sizeof(double) * p->n_packets));
+  }
+  // the carve-up adds at most 255 bytes of padding per array
+  return COLT_OK;
+}
+
+void free_tally(Tally* t) {
+  if (t->block) cudaFreeAsync(t->block, t->stream);
+  *t = Tally{};
+}
+
+// Job description from a grid and parameters (tally pointers filled later).
+RunDev make_run(const GridObj& g, const colt_run_params* p) {
+  RunDev r;
+  r.n_packets = p->n_packets;
+  r.pid_offset = p->pid_offset;
+  r.rng = Rng{uint32_t(p->seed), uint32_t(p->seed >> 32)};
+  for (int a = 0; a < 3; ++a) r.src[a] = p->src_pos[a];
+  r.src_sigma = p->src_sigma;
+  r.core_skip = p->core_skip ? 1 : 0;
+  r.recoil = p->recoil ? 1 : 0;
+  r.phase = p->phase;
+  r.tau_max = p->tau_esc_max;
+  r.albedo = p->albedo;
+  r.max_scatter = p->max_scatter;
+  const double vref = p->T_ref > 0 ? vth_kms(p->T_ref) : 1.0;
+  r.spec_scale = p->spec_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
+  r.spec_lo = p->spec_lo;
+  r.spec_hi = p->spec_hi;
+  r.spec_nb = p->spec_nbins;
+  r.n_cam = p->n_cam;
+  int64_t off = 0;
+  for (int i = 0; i < p->n_cam; ++i) {
+    camera_axis(p->cams[i].dir, &r.cam[i].axis, &r.cam[i].sgn);
+    r.cam[i].npix = p->cams[i].npix;
+    r.cam[i].img_off = off;
+    off += (int64_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
+  }
+  r.cam_scale = p->cam_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
+  r.cam_lo = p->cam_lo;
+  r.cam_hi = p->cam_hi;
+  r.cam_nb = p->cam_nbins > 0 ? p->cam_nbins : 1;
+  double fov = 0;
+  for (int a = 0; a < 3; ++a) {
+    r.centre[a] = 0.5 * (g.dev.lo[a] + g.dev.hi[a]);
+    fov = std::max(fov, 0.5 * (g.dev.hi[a] - g.dev.lo[a]));
+  }
+  r.fov_half = p->fov_half > 0 ? p->fov_half : fov;
+  return r;
+}
+
+void attach_tally(RunDev* r, const Tally& t) {
+  r->t.spec = t.spec;
+  r->t.counters = t.counters;
+  r->t.cam_spec = t.cam_spec;
+  r->t.cam_spec2 = t.cam_spec2;
+  r->t.cam_image = t.cam_image;
+  r->t.pk_status = t.pk_status;
+  r->t.pk_nscat = t.pk_nscat;
+  r->t.pk_freq = t.pk_freq;
+}
+
+int ensure_launch_buf(colt_ctx* ctx) {
+  LaunchBuf& lb = ctx->lb;
+  if (lb.host) return COLT_OK;
+  lb.bytes = lb.off_jobs() + sizeof(Job) * kMaxJobs;
+  CU(cudaMallocHost(&lb.host, lb.bytes));
+  CU(cudaMalloc(&lb.dev, lb.bytes));
+  CU(cudaMalloc(&lb.work, sizeof(unsigned long long) * 8));
+  CU(cudaMalloc(&lb.error, sizeof(int)));
+  CU(cudaMemset(lb.error, 0, sizeof(int)));
+  std::memset(lb.host, 0, lb.bytes);
+  LaunchDev* h = lb.hdr_h();
+  h->jobs = reinterpret_cast<const Job*>(lb.dev + lb.off_jobs());
+  h->job_end = reinterpret_cast<const unsigned long long*>(lb.dev + lb.off_end());
+  h->next = lb.work;
+  h->counters = lb.work + 1;
+  h->error = lb.error;
+  return COLT_OK;
+}
+
+// Enqueue one persistent launch over the jobs staged in lb.host:
+// header/job table copy, counter reset, kernel.  Recorded once per precision
+// as a CUDA graph and replayed.
+int enqueue_launch(colt_ctx* ctx, int precision, int blocks_per_sm) {
+  LaunchBuf& lb = ctx->lb;
+  const int gi = precision == COLT_PLAIN ? 0 : 1;
+  if (blocks_per_sm > 0) {
+    CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, ctx->stream));
+    CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, blocks_per_sm, ctx->sm_count,
+                        ctx->stream));
+    return COLT_OK;
+  }
+  if (!ctx->graph[gi]) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, ctx->stream);
+    cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, 0, ctx->sm_count,
+                                      ctx->stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+    if (le != cudaSuccess) return cuda_fail(ctx, le, "transport launch (capture)");
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&ctx->graph[gi], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+  }
+  CU(cudaGraphLaunch(ctx->graph[gi], ctx->stream));
+  return COLT_OK;
+}
+
+int check_device_error(colt_ctx* ctx) {
+  int h = 0;
+  if (!ctx->lb.error) return COLT_OK;
+  CU(cudaMemcpyAsync(&h, ctx->lb.error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    CU(cudaMemsetAsync(ctx->lb.error, 0, sizeof(int), ctx->stream));
+    return fail(ctx, COLT_EDEVICE, "transport kernel raised its error flag (cell index out of range)");
+  }
+  return COLT_OK;
+}
+
+// Copy a request's tallies into a caller's colt_result.
+int copy_result(colt_ctx* ctx, const colt_run_params* p, const Tally& t, colt_result* out, bool per_packet) {
+  unsigned long long cnt[kNumCounters];
+  CU(cudaMemcpyAsync(cnt, t.counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
+  if (out->spec)
+    CU(cudaMemcpyAsync(out->spec, t.spec, sizeof(uint64_t) * p->spec_nbins, cudaMemcpyDeviceToHost, ctx->stream));
+  if (p->n_cam > 0) {
+    const size_t ns = (size_t)p->n_cam * p->cam_nbins;
+    if (out->cam_spec) CU(cudaMemcpyAsync(out->cam_spec, t.cam_spec, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->cam_spec2) CU(cudaMemcpyAsync(out->cam_spec2, t.cam_spec2, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->cam_image && t.cam_image) {
+      size_t img = 0;
+      for (int i = 0; i < p->n_cam; ++i) img += (size_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
+      CU(cudaMemcpyAsync(out->cam_image, t.cam_image, sizeof(double) * img, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  if (per_packet) {
+    if (out->pk_status) CU(cudaMemcpyAsync(out->pk_status, t.pk_status, sizeof(int32_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->pk_nscat) CU(cudaMemcpyAsync(out->pk_nscat, t.pk_nscat, sizeof(uint64_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->pk_freq) CU(cudaMemcpyAsync(out->pk_freq, t.pk_freq, sizeof(double) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  out->n_emitted = cnt[kEmitted];
+  out->n_escaped = cnt[kEscaped];
+  out->n_absorbed = cnt[kAbsorbed];
+  out->n_capped = cnt[kCapped];
+  out->n_scat = cnt[kScat];
+  out->n_scat_hi = cnt[kScatHI];
+  out->spec_under = cnt[kUnder];
+  out->spec_over = cnt[kOver];
+  return COLT_OK;
+}
+
+int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
+  if (!d) return fail(ctx, COLT_EINVAL, "desc is NULL");
+  if (d->kind != COLT_CARTESIAN) return fail(ctx, COLT_EINVAL, "octree grids are not supported by this build");
+  if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(ctx, COLT_EINVAL, "cell counts must be positive");
+  const int64_t n = (int64_t)d->nx * d->ny * d->nz;
+  if (n > (int64_t)1 << 31) return fail(ctx, COLT_EINVAL, "too many cells");
+  for (int a = 0; a < 3; ++a)
+    if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->lo[a]) || !std::isfinite(d->hi[a]))
+      return fail(ctx, COLT_EINVAL, "box must have hi > lo");
+  if (!d->n_HI || !d->T || !d->vx || !d->vy || !d->vz) return fail(ctx, COLT_EINVAL, "missing field array");
+  if (!(d->f_nl >= 0)) return fail(ctx, COLT_EINVAL, "f_nl must be >= 0");
+  // fields to host
+  std::vector<float> hf[6];
+  const float* src[6] = {d->n_HI, d->T, d->vx, d->vy, d->vz, d->k_dust};
+  const float* f[6];
+  for (int i = 0; i < 6; ++i) {
+    if (!src[i]) { f[i] = nullptr; continue; }
+    if (d->fields_mem == COLT_MEM_DEVICE) {
+      hf[i].resize(n);
+      CU(cudaMemcpy(hf[i].data(), src[i], sizeof(float) * n, cudaMemcpyDeviceToHost));
+      f[i] = hf[i].data();
+    } else {
+      f[i] = src[i];
+    }
+  }
+  const size_t bytes = sizeof(float4) * 2 * (size_t)n;
+  if (ctx->used + bytes > ctx->budget) return fail(ctx, COLT_ENOMEM, "grid exceeds the memory budget");
+  std::vector<float4> rec(2 * (size_t)n);
+  for (int64_t c = 0; c < n; ++c) {
+    const double T = f[1][c], nh = f[0][c];
+    if (!(T > 0) || !std::isfinite(T) || !(nh >= 0) || !std::isfinite(nh))
+      return fail(ctx, COLT_EINVAL, "T must be > 0 and n_HI >= 0 (finite) in every cell");
+    const double vth = vth_kms(T);
+    const double kd = f[5] ? (double)f[5][c] : 0.0;
+    if (!(kd >= 0) || !std::isfinite(kd)) return fail(ctx, COLT_EINVAL, "k_dust must be >= 0");
+    rec[2 * c] = make_float4((float)(nh * sigma0(T)), (float)damping_a(T), (float)kd, (float)(1.0 / vth));
+    rec[2 * c + 1] = make_float4((float)(f[2][c] / vth), (float)(f[3][c] / vth), (float)(f[4][c] / vth), 0.0f);
+  }
+  GridDev& G = g->dev;
+  G.kind = COLT_CARTESIAN;
+  G.n[0] = d->nx; G.n[1] = d->ny; G.n[2] = d->nz;
+  G.stride[0] = 1; G.stride[1] = d->nx; G.stride[2] = (int64_t)d->nx * d->ny;
+  for (int a = 0; a < 3; ++a) {
+    G.lo[a] = d->lo[a];
+    G.hi[a] = d->hi[a];
+    G.h[a] = (d->hi[a] - d->lo[a]) / G.n[a];
+  }
+  G.periodic_xy = d->periodic_xy ? 1 : 0;
+  G.n_cells = n;
+  CU(cudaMalloc(&g->rec, bytes));
+  CU(cudaMemcpyAsync(g->rec, rec.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+  G.rec = g->rec;
+  // non-local a tau (Eq. atauNL), once per grid
+  float* dn = nullptr;
+  CU(cudaMalloc(&dn, sizeof(float) * n));
+  CU(cudaMemcpyAsync(dn, f[0], sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+  cudaError_t e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFree(dn);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "atau_nl kernel");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "atau_nl sync");
+  g->bytes = bytes;
+  return COLT_OK;
+}
+
+// ----------------------------------------------------------- serving core --
+int serve_complete_step(colt_ctx* ctx) {
+  // called once the in-flight step has finished on the device
+  ctx->step_in_flight = false;
+  const double t = now_ms();
+  for (auto& jp : ctx->step_jobs) {
+    auto it = ctx->reqs.find(jp.first);
+    if (it == ctx->reqs.end()) continue;
+    Req& r = *it->second;
+    r.done_packets += jp.second;
+    r.in_flight = 0;
+    if (r.done_packets >= r.p.n_packets && r.state == kAdmitted) {
+      r.state = kDone;
+      r.t_done = t;
+    }
+  }
+  ctx->step_jobs.clear();
+  return check_device_error(ctx);
+}
+
+int serve_admit(colt_ctx* ctx) {
+  int admitted = 0;
+  while (!ctx->queue.empty()) {
+    int active = 0;
+    for (auto& kv : ctx->reqs) active += kv.second->state == kAdmitted;
+    if (active >= kMaxJobs) break;
+    const uint64_t id = ctx->queue.front();
+    auto it = ctx->reqs.find(id);
+    if (it == ctx->reqs.end()) { ctx->queue.pop_front(); continue; }
+    Req& r = *it->second;
+    if (ctx->used + r.need_bytes > ctx->budget) break;   // FIFO: wait for memory
+    int rc = alloc_tally(ctx, &r.p, false, &r.tally);
+    if (rc) return rc;
+    ctx->used += r.tally.bytes;
+    attach_tally(&r.run, r.tally);
+    r.state = kAdmitted;
+    ctx->queue.pop_front();
+    ++admitted;
+  }
+  return admitted;
+}
+
+// Build and enqueue one batched step over admitted requests (oldest first),
+// sharing a packet budget; all jobs of a step share one precision.
+int serve_launch_step(colt_ctx* ctx) {
+  std::vector<Req*> act;
+  for (auto& kv : ctx->reqs)
+    if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->p.n_packets) act.push_back(kv.second.get());
+  if (act.empty()) return 0;
+  std::sort(act.begin(), act.end(), [](Req* a, Req* b) { return a->id < b->id; });
+  const int prec = act.front()->p.precision;
+  std::vector<Req*> sel;
+  for (Req* r : act)
+    if (r->p.precision == prec && (int)sel.size() < kMaxJobs) sel.push_back(r);
+  // fair share of the step budget, at least 1 packet each
+  uint64_t left = kStepPackets;
+  const uint64_t share = std::max<uint64_t>(1, kStepPackets / sel.size());
+  LaunchBuf& lb = ctx->lb;
+  int rc = ensure_launch_buf(ctx);
+  if (rc) return rc;
+  unsigned long long total = 0;
+  int nj = 0;
+  ctx->step_jobs.clear();
+  for (Req* r : sel) {
+    const uint64_t rem = r->p.n_packets - r->next_local;
+    uint64_t take = std::min<uint64_t>(rem, std::max<uint64_t>(share, left / std::max<size_t>(1, sel.size() - nj)));
+    if (take == 0) continue;
+    const GridObj& g = ctx->grids.at(r->grid);
+    Job& J = lb.jobs_h()[nj];
+    J.g = g.dev;
+    J.p = r->run;
+    J.p.n_packets = take;
+    J.p.pid_offset = r->run.pid_offset + r->next_local;
+    total += take;
+    lb.end_h()[nj] = total;
+    r->next_local += take;
+    r->in_flight = take;
+    ctx->step_jobs.push_back({r->id, take});
+    left = left > take ? left - take : 0;
+    ++nj;
+  }
+  LaunchDev* h = lb.hdr_h();
+  h->n_jobs = nj;
+  h->total = total;
+  rc = enqueue_launch(ctx, prec, 0);
+  if (rc) return rc;
+  CU(cudaEventRecord(ctx->ev_step, ctx->stream));
+  ctx->step_in_flight = true;
+  return 1;
+}
+
+// Advance the scheduler without blocking on the device.
+int serve_pump(colt_ctx* ctx) {
+  if (ctx->step_in_flight) {
+    cudaError_t q = cudaEventQuery(ctx->ev_step);
+    if (q == cudaErrorNotReady) return COLT_OK;
+    if (q != cudaSuccess) return cuda_fail(ctx, q, "serving step");
+    int rc = serve_complete_step(ctx);
+    if (rc) return rc;
+  }
+  int rc = serve_admit(ctx);
+  if (rc < 0) return rc;
+  rc = serve_launch_step(ctx);
+  return rc < 0 ? rc : COLT_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI ==
+extern "C" {
+
+int colt_init(colt_ctx** out, int device, size_t mem_budget_bytes, void* cuda_stream) {
+  if (!out) return COLT_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0 || device < 0 || device >= n) return COLT_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return COLT_ECUDA;
+  auto* ctx = new colt_ctx();
+  ctx->device = device;
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete ctx; return COLT_ECUDA; }
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->l2 = prop.l2CacheSize;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)fr);
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return COLT_ECUDA; }
+    ctx->own_stream = true;
+  }
+  // keep freed tally blocks cached in the device's default pool
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaEventCreate(&ctx->ev0);
+  cudaEventCreate(&ctx->ev1);
+  cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming);
+  *out = ctx;
+  return COLT_OK;
+}
+
+void colt_finalize(colt_ctx* ctx) {
+  if (!ctx) return;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->reqs) free_tally(&kv.second->tally);
+    for (auto& kv : ctx->grids) cudaFree(kv.second.rec);
+    for (auto& g : ctx->graph) if (g) cudaGraphExecDestroy(g);
+    if (ctx->lb.host) cudaFreeHost(ctx->lb.host);
+    if (ctx->lb.dev) cudaFree(ctx->lb.dev);
+    if (ctx->lb.work) cudaFree(ctx->lb.work);
+    if (ctx->lb.error) cudaFree(ctx->lb.error);
+    cudaEventDestroy(ctx->ev0);
+    cudaEventDestroy(ctx->ev1);
+    cudaEventDestroy(ctx->ev_step);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+const char* colt_last_error(colt_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int colt_device_info(colt_ctx* ctx, int* sm_count, size_t* l2_bytes, int* cc_major, int* cc_minor) {
+  if (!ctx) return COLT_EINVAL;
+  if (sm_count) *sm_count = ctx->sm_count;
+  if (l2_bytes) *l2_bytes = ctx->l2;
+  if (cc_major) *cc_major = ctx->cc_major;
+  if (cc_minor) *cc_minor = ctx->cc_minor;
+  return COLT_OK;
+}
+
+int colt_create_grid(colt_ctx* ctx, const colt_grid_desc* desc, colt_grid* out) {
+  if (!ctx || !out) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  GridObj g;
+  int rc = build_grid(ctx, desc, &g);
+  if (rc) {
+    if (g.rec) cudaFree(g.rec);
+    return rc;
+  }
+  const uint64_t h = ctx->next_handle++;
+  ctx->grids[h] = g;
+  ctx->used += g.bytes;
+  *out = h;
+  return COLT_OK;
+}
+
+int colt_destroy_grid(colt_ctx* ctx, colt_grid grid) {
+  if (!ctx) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->grids.find(grid);
+  if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+  for (auto& kv : ctx->reqs)
+    if (kv.second->grid == grid && kv.second->state != kDone)
+      return fail(ctx, COLT_EINVAL, "grid is in use by an unfinished request");
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(it->second.rec);
+  ctx->used -= it->second.bytes;
+  ctx->grids.erase(it);
+  return COLT_OK;
+}
+
+int colt_read_cells(colt_ctx* ctx, colt_grid grid, float* out, size_t n_floats) {
+  if (!ctx || !out) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->grids.find(grid);
+  if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+  if (n_floats != 8 * (size_t)it->second.dev.n_cells) return fail(ctx, COLT_EINVAL, "n_floats must be 8 * n_cells");
+  CU(cudaMemcpyAsync(out, it->second.rec, sizeof(float) * n_floats, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return COLT_OK;
+}
+
+int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
+                   colt_result* out) {
+  if (!ctx || !grids || !params || !out || n < 1 || n > kMaxJobs) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const int prec = params[0].precision;
+  std::vector<const GridObj*> gs(n);
+  for (int i = 0; i < n; ++i) {
+    auto it = ctx->grids.find(grids[i]);
+    if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+    gs[i] = &it->second;
+    int rc = validate_params(ctx, it->second, &params[i]);
+    if (rc) return rc;
+    if (params[i].precision != prec) return fail(ctx, COLT_EINVAL, "all solves of a batch need one precision");
+  }
+  // a blocking run waits for any in-flight serving step first
+  if (ctx->step_in_flight) {
+    CU(cudaEventSynchronize(ctx->ev_step));
+    int rc = serve_complete_step(ctx);
+    if (rc) return rc;
+  }
+  std::vector<bool> per_packet(n);
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    per_packet[i] = out[i].pk_status || out[i].pk_nscat || out[i].pk_freq;
+    need += tally_bytes(&params[i], per_packet[i]) + 256;
+  }
+  if (ctx->used + need > ctx->budget) return fail(ctx, COLT_ENOMEM, "tallies exceed the memory budget");
+  std::vector<Tally> ts(n);
+  auto free_all = [&]() { for (auto& t : ts) free_tally(&t); };
+  int rc = ensure_launch_buf(ctx);
+  if (rc) return rc;
+  LaunchBuf& lb = ctx->lb;
+  unsigned long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    rc = alloc_tally(ctx, &params[i], per_packet[i], &ts[i]);
+    if (rc) { free_all(); return rc; }
+    Job& J = lb.jobs_h()[i];
+    J.g = gs[i]->dev;
+    J.p = make_run(*gs[i], &params[i]);
+    attach_tally(&J.p, ts[i]);
+    total += params[i].n_packets;
+    lb.end_h()[i] = total;
+  }
+  LaunchDev* h = lb.hdr_h();
+  h->n_jobs = n;
+  h->total = total;
+  unsigned long long lcnt[kNumLaunchCounters] = {0, 0, 0};
+  float ms = 0;
+  if (total > 0) {
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    rc = enqueue_launch(ctx, prec, params[0].blocks_per_sm);
+    if (rc) { free_all(); return rc; }
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    CU(cudaMemcpyAsync(lcnt, lb.work + 1, sizeof(lcnt), cudaMemcpyDeviceToHost, ctx->stream));
+    cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    if (se != cudaSuccess) { free_all(); return cuda_fail(ctx, se, "transport kernel"); }
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  }
+  rc = check_device_error(ctx);
+  for (int i = 0; i < n && !rc; ++i) {
+    rc = copy_result(ctx, &params[i], ts[i], &out[i], per_packet[i]);
+    out[i].kernel_ms = ms;
+    out[i].n_cell_visits = lcnt[kCellVisits];
+    out[i].n_peel_visits = lcnt[kPeelVisits];
+    out[i].n_peel_rays = lcnt[kPeelRays];
+  }
+  free_all();
+  return rc;
+}
+
+int colt_run(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_result* out) {
+  if (!ctx || !out || !p) return COLT_EINVAL;
+  return colt_run_batch(ctx, 1, &grid, p, out);
+}
+
+int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params* p, colt_result* out) {
+  if (!ctx) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  colt_grid g = 0;
+  int rc = colt_create_grid(ctx, desc, &g);
+  if (rc) return rc;
+  rc = colt_run(ctx, g, p, out);
+  colt_destroy_grid(ctx, g);
+  return rc;
+}
+
+int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out) {
+  if (!ctx || !out) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  auto it = ctx->grids.find(grid);
+  if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+  int rc = validate_params(ctx, it->second, p);
+  if (rc) return rc;
+  if (ctx->queue.size() >= 4096) return fail(ctx, COLT_EAGAIN, "request queue full");
+  auto r = std::make_unique<Req>();
+  r->id = ctx->next_handle++;
+  r->grid = grid;
+  r->p = *p;
+  r->cams.assign(p->cams, p->cams + p->n_cam);
+  r->p.cams = r->cams.data();
+  r->need_bytes = tally_bytes(&r->p, false);
+  size_t grids_bytes = 0;
+  for (auto& kv : ctx->grids) grids_bytes += kv.second.bytes;
+  if (grids_bytes + r->need_bytes > ctx->budget)
+    return fail(ctx, COLT_ENOMEM, "request can never fit in the memory budget");
+  r->run = make_run(it->second, &r->p);
+  r->t_submit = now_ms();
+  if (r->p.n_packets == 0) { r->state = kDone; r->t_done = r->t_submit; }
+  else ctx->queue.push_back(r->id);
+  *out = r->id;
+  ctx->reqs[r->id] = std::move(r);
+  return serve_pump(ctx);
+}
+
+int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
+  if (!ctx) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  int rc = serve_pump(ctx);
+  if (rc) return rc;
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  const Req& r = *it->second;
+  if (done) *done = r.state == kDone;
+  if (st) {
+    st->done = r.state == kDone;
+    st->admitted = r.state != kQueued;
+    st->packets_done = r.done_packets;
+    st->packets_total = r.p.n_packets;
+    st->submit_to_done_ms = r.state == kDone ? r.t_done - r.t_submit : 0.0;
+  }
+  return COLT_OK;
+}
+
+int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms) {
+  if (!ctx) return COLT_EINVAL;
+  const double t0 = now_ms();
+  for (;;) {
+    int done = 0;
+    {
+      std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+      int rc = colt_poll(ctx, req, &done, nullptr);
+      if (rc) return rc;
+      if (done) return COLT_OK;
+      if (ctx->step_in_flight) {
+        // block on the in-flight step (bounded: one batched launch)
+        cudaError_t e = cudaEventSynchronize(ctx->ev_step);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "serving step");
+      }
+    }
+    if (timeout_ms >= 0 && now_ms() - t0 > timeout_ms) return fail(ctx, COLT_ETIMEOUT, "colt_wait timed out");
+  }
+}
+
+int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out) {
+  if (!ctx || !out) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  Req& r = *it->second;
+  if (r.state != kDone) return fail(ctx, COLT_EAGAIN, "request not done");
+  if (!r.tally.block) {  // zero-packet request
+    colt_result z{};
+    z.spec = out->spec;
+    if (out->spec) std::memset(out->spec, 0, sizeof(uint64_t) * r.p.spec_nbins);
+    *out = z;
+    return COLT_OK;
+  }
+  out->pk_status = nullptr;
+  out->pk_nscat = nullptr;
+  out->pk_freq = nullptr;
+  int rc = copy_result(ctx, &r.p, r.tally, out, false);
+  out->kernel_ms = 0;
+  out->n_cell_visits = out->n_peel_visits = out->n_peel_rays = 0;
+  return rc;
+}
+
+int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t nbins) {
+  if (!ctx || !buf) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  Req& r = *it->second;
+  if (r.state != kDone) return fail(ctx, COLT_EAGAIN, "request not done");
+  if (camera < -1 || camera >= r.p.n_cam) return fail(ctx, COLT_EINVAL, "bad camera index");
+  if (camera == -1) {
+    if (nbins != (size_t)r.p.spec_nbins) return fail(ctx, COLT_EINVAL, "nbins mismatch");
+    std::vector<uint64_t> h(nbins, 0);
+    if (r.tally.block) {
+      CU(cudaMemcpyAsync(h.data(), r.tally.spec, sizeof(uint64_t) * nbins, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+    }
+    for (size_t i = 0; i < nbins; ++i) buf[i] = (double)h[i];
+  } else {
+    if (nbins != (size_t)r.p.cam_nbins) return fail(ctx, COLT_EINVAL, "nbins mismatch");
+    if (!r.tally.block) { std::memset(buf, 0, sizeof(double) * nbins); return COLT_OK; }
+    CU(cudaMemcpyAsync(buf, r.tally.cam_spec + (size_t)camera * r.p.cam_nbins, sizeof(double) * nbins,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  return COLT_OK;
+}
+
+int colt_release(colt_ctx* ctx, colt_req req) {
+  if (!ctx) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  Req& r = *it->second;
+  if (r.state == kAdmitted) return fail(ctx, COLT_EAGAIN, "request still running");
+  if (r.state == kQueued) {
+    ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), req), ctx->queue.end());
+  }
+  if (r.tally.block) {
+    cudaStreamSynchronize(ctx->stream);
+    ctx->used -= r.tally.bytes;
+    free_tally(&r.tally);
+  }
+  ctx->reqs.erase(it);
+  return COLT_OK;
+}
+
+int colt_voigt(colt_ctx* ctx, const void* a, const void* x, void* H, size_t n, int precision, int mem) {
+  if (!ctx || (n && (!a || !x || !H))) return COLT_EINVAL;
+  if (precision != COLT_PLAIN && precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const size_t es = precision == COLT_PLAIN ? sizeof(double) : sizeof(float);
+  if (mem == COLT_MEM_DEVICE) {
+    CU(launch_voigt(a, x, H, n, precision, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return COLT_OK;
+  }
+  void *da = nullptr, *dx = nullptr, *dh = nullptr;
+  CU(cudaMalloc(&da, es * n + 1));
+  CU(cudaMalloc(&dx, es * n + 1));
+  CU(cudaMalloc(&dh, es * n + 1));
+  cudaMemcpyAsync(da, a, es * n, cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(dx, x, es * n, cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e = launch_voigt(da, dx, dh, n, precision, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(H, dh, es * n, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFree(da);
+  cudaFree(dx);
+  cudaFree(dh);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "voigt kernel");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "voigt sync");
+  return COLT_OK;
+}
+
+int colt_scatter(colt_ctx* ctx, colt_scatter_io* io, size_t n, uint64_t seed, int precision) {
+  if (!ctx || (n && !io)) return COLT_EINVAL;
+  if (precision != COLT_PLAIN && precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  if (n == 0) return COLT_OK;
+  void* d = nullptr;
+  CU(cudaMalloc(&d, sizeof(colt_scatter_io) * n));
+  cudaMemcpyAsync(d, io, sizeof(colt_scatter_io) * n, cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e = launch_scatter(d, n, seed, precision, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(io, d, sizeof(colt_scatter_io) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter kernel");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "scatter sync");
+  return COLT_OK;
+}
+
+}  // extern "C"

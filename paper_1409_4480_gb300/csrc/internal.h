@@ -1,0 +1,111 @@
+// Internal structures shared by the library's translation units (not part of
+// the public ABI; see include/colt.h for that).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace colt {
+
+constexpr int kMaxCams = 8;
+
+// Per-cell record, two float4 (32 bytes, one DRAM/L2 sector):
+//   r0 = (k_HI = n_HI sigma_0 [1/cm], a, k_dust [1/cm], 1/v_th [s/km])
+//   r1 = (u_x, u_y, u_z [v/v_th], a tau_NL)
+// Cartesian cells are stored x-fastest; octree leaves in input order.
+struct GridDev {
+  const float4* rec = nullptr;
+  int kind = 0;
+  int n[3] = {0, 0, 0};
+  int64_t stride[3] = {1, 0, 0};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  int periodic_xy = 0;
+  int64_t n_cells = 0;
+  // octree (kind == 1)
+  const int32_t* node = nullptr;       // per node: >= 0 first child, < 0 -> leaf (-1 - leaf)
+  const int32_t* nbr = nullptr;        // per leaf: 6 face neighbours (node ids, same or coarser), -1 = outside
+  const uint8_t* leaf_level = nullptr;
+  const uint32_t* leaf_ijk = nullptr;  // 3 per leaf
+  int max_level = 0;
+};
+
+struct CamDev {
+  int axis = 0;      // 0,1,2
+  int sgn = 1;       // +1 / -1
+  int npix = 0;
+  int64_t img_off = 0;
+};
+
+struct Tallies {
+  unsigned long long* spec = nullptr;       // [spec_nb]
+  unsigned long long* counters = nullptr;   // [kNumCounters] (per job)
+  double* cam_spec = nullptr;               // [n_cam * cam_nb]
+  double* cam_spec2 = nullptr;
+  double* cam_image = nullptr;              // optional
+  int32_t* pk_status = nullptr;             // optional [n_packets]
+  uint64_t* pk_nscat = nullptr;
+  double* pk_freq = nullptr;
+};
+
+// per-job counters (packet outcomes)
+enum Counter {
+  kEmitted = 0, kEscaped, kAbsorbed, kCapped, kScat, kScatHI, kUnder, kOver, kNumCounters
+};
+// per-launch diagnostic counters
+enum LaunchCounter { kCellVisits = 0, kPeelVisits, kPeelRays, kNumLaunchCounters };
+
+struct RunDev {
+  uint64_t n_packets = 0;
+  uint64_t pid_offset = 0;    // packet ids are pid_offset + [0, n_packets)
+  Rng rng{0, 0};
+  double src[3] = {0, 0, 0};
+  double src_sigma = 0;
+  int core_skip = 1, recoil = 1, phase = 0;
+  double tau_max = 50.0;
+  double albedo = 0.0;
+  uint64_t max_scatter = ~0ull;
+  double spec_scale = 1.0;    // spectral coordinate = (lab Doppler velocity [km/s]) * scale
+  double spec_lo = 0, spec_hi = 1;
+  int spec_nb = 1;
+  int n_cam = 0;
+  CamDev cam[kMaxCams];
+  double cam_scale = 1.0;
+  double cam_lo = 0, cam_hi = 1;
+  int cam_nb = 1;
+  double fov_half = 1.0;
+  double centre[3] = {0, 0, 0};
+  Tallies t;
+};
+
+// One solve inside a launch: its grid, its parameters and its tallies.
+struct Job {
+  GridDev g;
+  RunDev p;
+};
+
+// A persistent launch over n_jobs jobs.  Packet slots are numbered 0..total-1
+// across jobs; job j owns [job_end[j-1], job_end[j]).
+struct LaunchDev {
+  const Job* jobs = nullptr;
+  const unsigned long long* job_end = nullptr;
+  int n_jobs = 0;
+  unsigned long long total = 0;
+  unsigned long long* next = nullptr;        // work counter
+  unsigned long long* counters = nullptr;    // [kNumLaunchCounters]
+  int* error = nullptr;                      // device-side error flag
+};
+
+// launchers (transport.cu)
+// L is a DEVICE pointer to the launch header (so a captured graph can replay it).
+cudaError_t launch_transport(const LaunchDev* L, int precision, int blocks_per_sm, int sm_count, cudaStream_t s);
+// persistent grid size the launcher uses for a precision
+int transport_grid_size(int precision, int blocks_per_sm, int sm_count);
+// grid preparation (grid.cu)
+cudaError_t launch_atau_nl(const GridDev& g, const float* n_hi, double f_nl, float4* rec_mut, cudaStream_t s);
+// parity helpers (parity.cu)
+cudaError_t launch_voigt(const void* a, const void* x, void* H, size_t n, int precision, cudaStream_t s);
+struct ScatterIODev;
+cudaError_t launch_scatter(void* io, size_t n, uint64_t seed, int precision, cudaStream_t s);
+
+}  // namespace colt

@@ -1,0 +1,496 @@
+// Persistent photon-packet transport kernel (Cartesian grids).
+//
+// Paper mapping:
+//   emission           Sec. 3.1.1 (isotropic k_i, x_i = 0 in the source cell)
+//   tau_event = -ln R  Sec. 3.1.2, Eq. lnR
+//   cell march         Sec. 3.1.2 (tau_cell = (n sigma_0 H(a,x) + k_dust) l_cell,
+//                      x' = (x + k.u) sqrt(T/T') - k.u' at every face)
+//   scattering         Sec. 3.1.3 + 3.2.3 + 3.2.4 (device.cuh: scatter_hi)
+//   peel-off           Sec. 6.1, Eq. SB (W(theta) exp(-tau_esc), stop at tau_esc > 50)
+//
+// GB300 design:
+//   * One packet per lane; lanes whose packet finished take the next packet
+//     slot from a global counter at the top of every round (one warp-aggregated
+//     atomic per refill), so warps never idle on short packets.  Slots are
+//     numbered across all jobs of the launch (a job = one solve: grid, params,
+//     tallies), so one persistent launch runs many heterogeneous requests.
+//   * A round advances every live lane by one flight + one interaction; the
+//     march is per lane in cell-local coordinates (FP32 in the mixed path), with
+//     the remaining optical depth in FP64.
+//   * Peel-off rays run along coordinate axes.  Their cell sequence is known in
+//     advance and the lab-frame frequency (x + k.u) v_th is invariant along a
+//     ray, so the whole warp marches one ray at a time, 32 cells per step
+//     (coalesced 32-byte records), with a butterfly sum of the cell optical
+//     depths and an early exit once tau_esc exceeds the cutoff.
+//   * Tally atomics are staged one per lane and issued 32 at a time.
+#include "internal.h"
+
+namespace colt {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kMaxFlightVisits = 1u << 24;
+// recoil parameter over damping parameter: 2.536e-4 / 4.702e-4 (Sec. 2, Eq. recoil)
+constexpr double kGoverA = 2.536e-4 / 4.702e-4;
+
+template <typename R>
+struct PeelEv {
+  double pos[3];
+  int64_t cell;
+  int ijk[3];
+  int job;
+  R xi[3];
+  R x;          // comoving frequency at the event (before the scattering)
+  R k[3];       // incoming direction (HI scattering)
+  R ua[3];      // atom velocity (HI scattering)
+  R upar, g, RQ;
+  R inv_vth, u[3];
+  int type;     // 0: isotropic with W = 1 and x unchanged (emission, dust); 1: HI
+};
+
+__device__ __forceinline__ int bin_of(double s, double lo, double hi, int nb) {
+  if (!(s >= lo) || !(s < hi)) return -1;
+  int b = (int)floor((s - lo) * (double)nb / (hi - lo));
+  return (b >= 0 && b < nb) ? b : -1;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int64_t cell_index(const GridDev& G, const int c3[3]) {
+  return (int64_t)c3[0] + G.stride[1] * c3[1] + G.stride[2] * c3[2];
+}
+
+template <typename R, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32)
+k_transport(const LaunchDev* __restrict__ Lp) {
+  const LaunchDev L = *Lp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PeelEv<R>* sev = reinterpret_cast<PeelEv<R>*>(smem_raw) + (threadIdx.x >> 5) * 32;
+  const int lane = threadIdx.x & 31;
+
+  unsigned long long lc[kNumLaunchCounters] = {0, 0, 0};
+
+  // lane packet state
+  bool alive = false, done = false;
+  int jb = 0;
+  const Job* J = L.jobs;
+  uint64_t pid = 0;
+  uint32_t event = 0, nscat = 0, nscat_hi = 0;
+  int ci[3] = {0, 0, 0};
+  R xi[3] = {0, 0, 0};
+  R k[3] = {0, 0, 1};
+  R x = 0;
+  double tau = 0;
+
+  // staged peel-off tallies
+  double* st_spec = nullptr;
+  double* st_spec2 = nullptr;
+  double* st_img = nullptr;
+  double st_w = 0;
+  int nq = 0;
+
+  auto flush = [&](int upto) {
+    if (lane < upto && st_spec) {
+      atomicAdd(st_spec, st_w);
+      atomicAdd(st_spec2, st_w * st_w);
+      if (st_img) atomicAdd(st_img, st_w);
+    }
+    st_spec = nullptr;
+    st_img = nullptr;
+  };
+
+  auto finish = [&](int status, double sfreq) {
+    const RunDev& P = J->p;
+    unsigned long long* C = P.t.counters;
+    atomicAdd(C + kEmitted, 1ull);
+    if (status == 1) {
+      atomicAdd(C + kEscaped, 1ull);
+      const int b = bin_of(sfreq, P.spec_lo, P.spec_hi, P.spec_nb);
+      if (b >= 0) atomicAdd(P.t.spec + b, 1ull);
+      else if (sfreq < P.spec_lo) atomicAdd(C + kUnder, 1ull);
+      else atomicAdd(C + kOver, 1ull);
+    } else if (status == 2) {
+      atomicAdd(C + kAbsorbed, 1ull);
+    } else {
+      atomicAdd(C + kCapped, 1ull);
+    }
+    if (nscat) atomicAdd(C + kScat, (unsigned long long)nscat);
+    if (nscat_hi) atomicAdd(C + kScatHI, (unsigned long long)nscat_hi);
+    if (P.t.pk_status) {
+      P.t.pk_status[pid] = status;
+      P.t.pk_nscat[pid] = nscat;
+      P.t.pk_freq[pid] = status == 1 ? sfreq : 0.0;
+    }
+    alive = false;
+  };
+
+  auto fill_event = [&](int type, const R* kin, const R* ua, R upar, R g, R RQ, R xin, const float4& r0,
+                        const float4& r1) {
+    const GridDev& G = J->g;
+    PeelEv<R>& e = sev[lane];
+    e.type = type;
+    e.job = jb;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      e.ijk[a] = ci[a];
+      e.xi[a] = xi[a];
+      e.pos[a] = G.lo[a] + ((double)ci[a] + (double)xi[a]) * G.h[a];
+      e.k[a] = kin ? kin[a] : R(0);
+      e.ua[a] = ua ? ua[a] : R(0);
+    }
+    e.cell = cell_index(G, ci);
+    e.x = xin;
+    e.upar = upar;
+    e.g = g;
+    e.RQ = RQ;
+    e.inv_vth = r0.w;
+    e.u[0] = r1.x; e.u[1] = r1.y; e.u[2] = r1.z;
+  };
+
+  for (;;) {
+    bool has_peel = false;
+    // ---------------------------------------------------------- refill --
+    const unsigned need = __ballot_sync(kFull, !alive && !done);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(L.next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!alive && !done) {
+        const unsigned long long slot = base + __popc(need & ((1u << lane) - 1u));
+        if (slot < L.total) {
+          // job owning this slot
+          int lo = 0, hi = L.n_jobs - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (slot < L.job_end[mid]) hi = mid; else lo = mid + 1;
+          }
+          jb = lo;
+          J = L.jobs + jb;
+          const GridDev& G = J->g;
+          const RunDev& P = J->p;
+          // ---------------------------------------- emission, event 0 --
+          pid = slot - (jb ? L.job_end[jb - 1] : 0ull);
+          event = 0;
+          nscat = 0;
+          nscat_hi = 0;
+          const uint64_t rpid = pid + P.pid_offset;
+          U4<R> b0 = uniforms<R>(P.rng, rpid, 0, 0);
+          const R mu = R(2) * b0.v[0] - R(1);
+          R sp, cp;
+          m_sincospi(R(2) * b0.v[1], &sp, &cp);
+          const R st = m_sqrt(fmax(R(0), R(1) - mu * mu));
+          k[0] = st * cp; k[1] = st * sp; k[2] = mu;
+          tau = -log((double)b0.v[2]);
+          double r[3] = {P.src[0], P.src[1], P.src[2]};
+          if (P.src_sigma > 0.0) {
+            U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
+            const double rho1 = sqrt(-2.0 * log(b1.v[0])), rho2 = sqrt(-2.0 * log(b1.v[2]));
+            double s1, c1, s2, c2;
+            sincospi(2.0 * b1.v[1], &s1, &c1);
+            sincospi(2.0 * b1.v[3], &s2, &c2);
+            r[0] += P.src_sigma * rho1 * c1;
+            r[1] += P.src_sigma * rho1 * s1;
+            r[2] += P.src_sigma * rho2 * c2;
+          }
+          bool inside = true;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const double t = (r[a] - G.lo[a]) / G.h[a];
+            const double f = floor(t);
+            int i = 0;
+            R loc = R(0);
+            const bool in_range = f >= -1.0 && f <= (double)G.n[a];
+            if (in_range) {
+              i = (int)f;
+              loc = R(t - f);
+              if (t == f && k[a] < R(0)) { i -= 1; loc = R(1); }
+            }
+            if (!in_range || i < 0 || i >= G.n[a]) { inside = false; i = 0; }
+            ci[a] = i;
+            xi[a] = loc;
+          }
+          x = R(0);
+          alive = true;
+          if (!inside) {
+            finish(1, 0.0);     // source outside the box: leaves at line centre
+          } else if (P.n_cam > 0) {
+            const int64_t c = cell_index(G, ci);
+            fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, __ldg(G.rec + 2 * c), __ldg(G.rec + 2 * c + 1));
+            has_peel = true;
+          }
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(kFull, done)) break;
+
+    // ------------------------------------------------ flight + interaction --
+    // (a packet emitted this round makes its first flight next round)
+    if (alive && !(need & (1u << lane))) {
+      const GridDev& G = J->g;
+      const RunDev& P = J->p;
+      const float4* __restrict__ rec = G.rec;
+      const uint64_t rpid = pid + P.pid_offset;
+      R hh[3], ik[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        hh[a] = R(G.h[a]);
+        ik[a] = k[a] != R(0) ? R(1) / k[a] : R(0);
+      }
+      int64_t c = cell_index(G, ci);
+      float4 r0 = __ldg(rec + 2 * c), r1 = __ldg(rec + 2 * c + 1);
+      R ktot = 0;
+      bool interact = false, escaped = false;
+      int status = 0;
+      uint32_t visits = 0;
+      for (;;) {
+        if (++visits > kMaxFlightVisits) { status = 3; break; }
+        const R H = voigt<R>(R(r0.y), x);
+        ktot = R(r0.x) * H + R(r0.z);
+        // distance to the exit face (cm)
+        R tmin = R(3.0e38);
+        int ax = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (k[a] != R(0)) {
+            R d = (k[a] > R(0) ? (R(1) - xi[a]) : -xi[a]) * hh[a] * ik[a];
+            if (d < R(0)) d = R(0);
+            if (d < tmin) { tmin = d; ax = a; }
+          }
+        }
+        const double tau_cell = (double)(ktot * tmin);
+        if (tau <= tau_cell) {
+          const R le = R(tau) / ktot;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) xi[a] += le * k[a] / hh[a];
+          interact = true;
+          break;
+        }
+        tau -= tau_cell;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a != ax) xi[a] += tmin * k[a] / hh[a];
+        // cross the face on axis ax
+        const int sgn = k[ax] > R(0) ? 1 : -1;
+        int ni = ci[ax] + sgn;
+        xi[ax] = sgn > 0 ? R(0) : R(1);
+        if (ni < 0 || ni >= G.n[ax]) {
+          if (G.periodic_xy && ax < 2) {
+            ni = ni < 0 ? G.n[ax] - 1 : 0;
+          } else {
+            escaped = true;
+            break;
+          }
+        }
+        ci[ax] = ni;
+        const R ku_old = k[0] * R(r1.x) + k[1] * R(r1.y) + k[2] * R(r1.z);
+        const R ivth_old = R(r0.w);
+        c = cell_index(G, ci);
+        if (c < 0 || c >= G.n_cells) { atomicExch(L.error, 1); status = 3; break; }
+        r0 = __ldg(rec + 2 * c);
+        r1 = __ldg(rec + 2 * c + 1);
+        const R ku_new = k[0] * R(r1.x) + k[1] * R(r1.y) + k[2] * R(r1.z);
+        x = (x + ku_old) * (R(r0.w) / ivth_old) - ku_new;
+      }
+      lc[kCellVisits] += visits;
+      if (status == 3) {
+        finish(3, 0.0);
+      } else if (escaped) {
+        // lab-frame escape frequency in FP64: Doppler velocity (x + k.u) v_th
+        const double ku = (double)k[0] * r1.x + (double)k[1] * r1.y + (double)k[2] * r1.z;
+        const double V = ((double)x + ku) / (double)r0.w;
+        finish(1, V * P.spec_scale);
+      } else if (interact) {
+        ++event;
+        U4<R> b0 = uniforms<R>(P.rng, rpid, event, 0);
+        const R a = R(r0.y);
+        bool cont = true;
+        if (b0.v[0] * ktot < R(r0.z)) {
+          // dust: absorb with probability 1 - A, else isotropic scattering
+          if ((double)b0.v[1] >= P.albedo) {
+            finish(2, 0.0);
+            cont = false;
+          } else {
+            U4<R> b1 = uniforms<R>(P.rng, rpid, event, 1);
+            if (P.n_cam > 0) {
+              fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, r0, r1);
+              has_peel = true;
+            }
+            const R m = R(2) * b1.v[2] - R(1);
+            R sp, cp;
+            m_sincospi(R(2) * b1.v[3], &sp, &cp);
+            const R sm = m_sqrt(fmax(R(0), R(1) - m * m));
+            k[0] = sm * cp; k[1] = sm * sp; k[2] = m;
+            ++nscat;
+          }
+        } else {
+          R atau0 = R(-1);
+          if (P.core_skip) {
+            R lmin = R(3.0e38);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) lmin = fmin(lmin, fmin(xi[q], R(1) - xi[q]) * hh[q]);
+            lmin = fmax(lmin, R(0));
+            atau0 = a * R(r0.x) * lmin + R(r1.w);
+          }
+          const R g = P.recoil ? R(kGoverA) * a : R(0);
+          ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3]);
+          if (so.n_trials > kMaxTrials) {
+            finish(3, 0.0);
+            cont = false;
+          } else {
+            ++nscat;
+            ++nscat_hi;
+            if (P.n_cam > 0) {
+              fill_event(1, k, so.u_atom, so.u_par, g, so.RQ, x, r0, r1);
+              has_peel = true;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) k[q] = so.k_f[q];
+            x = so.x_f;
+          }
+        }
+        if (cont) {
+          if (P.max_scatter && nscat >= P.max_scatter) {
+            finish(3, 0.0);
+          } else {
+            tau = -log((double)b0.v[2]);
+          }
+        }
+      }
+    }
+
+    // ------------------------------------------------------------ peel-off --
+    unsigned pm = __ballot_sync(kFull, has_peel);
+    __syncwarp();
+    while (pm) {
+      const int src = __ffs(pm) - 1;
+      pm &= pm - 1;
+      const PeelEv<R>& e = sev[src];
+      const Job* JE = L.jobs + e.job;
+      const GridDev& G = JE->g;
+      const RunDev& P = JE->p;
+      const float4* __restrict__ rec = G.rec;
+      for (int cam = 0; cam < P.n_cam; ++cam) {
+        const int ax = P.cam[cam].axis;
+        const int s = P.cam[cam].sgn;
+        if (G.periodic_xy && ax < 2) continue;   // no observer along a periodic axis
+        R W = R(1), xc = e.x;
+        if (e.type == 1) {
+          const R mu_c = s > 0 ? e.k[ax] : -e.k[ax];
+          W = (R(1) + e.RQ * mu_c * mu_c) / (R(1) + e.RQ / R(3));
+          const R kcu = s > 0 ? e.ua[ax] : -e.ua[ax];
+          xc = e.x + kcu - e.upar + e.g * (mu_c - R(1));
+        }
+        const R us = s > 0 ? e.u[ax] : -e.u[ax];
+        // lab-frame Doppler velocity (km/s), invariant along the ray
+        const double V = ((double)xc + (double)us) / (double)e.inv_vth;
+        const int b = bin_of(V * P.cam_scale, P.cam_lo, P.cam_hi, P.cam_nb);
+        if (b < 0) continue;
+        const R Vr = (R)V;
+        const int start = e.ijk[ax];
+        const int remaining = s > 0 ? G.n[ax] - start : start + 1;
+        const int64_t step = (int64_t)s * G.stride[ax];
+        const R hax = R(G.h[ax]);
+        const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
+        double tau_acc = 0.0;
+        bool cut = false;
+        for (int base = 0; base < remaining; base += 32) {
+          const int m = base + lane;
+          R tc = R(0);
+          if (m < remaining) {
+            const int64_t c = e.cell + step * m;
+            const float4 q0 = __ldg(rec + 2 * c);
+            const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * c + 1) + ax);
+            const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
+            const R Hc = voigt<R>(R(q0.y), xcell);
+            tc = (R(q0.x) * Hc + R(q0.z)) * (m == 0 ? l0 : hax);
+            lc[kPeelVisits]++;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(kFull, tc, o);
+          tc = __shfl_sync(kFull, tc, 0);
+          tau_acc += (double)tc;
+          if (tau_acc > P.tau_max) { cut = true; break; }
+        }
+        if (lane == 0) lc[kPeelRays]++;
+        if (cut) continue;
+        const double w = (double)W * exp(-tau_acc);
+        // stage the tally on lane nq % 32
+        if (lane == (nq & 31)) {
+          const int64_t si = (int64_t)cam * P.cam_nb + b;
+          st_spec = P.t.cam_spec + si;
+          st_spec2 = P.t.cam_spec2 + si;
+          st_img = nullptr;
+          const int np = P.cam[cam].npix;
+          if (np > 0 && P.t.cam_image) {
+            const int au = (ax + 1) % 3, av = (ax + 2) % 3;
+            const double pu = s * (e.pos[au] - P.centre[au]);
+            const double pv = e.pos[av] - P.centre[av];
+            const double fu = (pu + P.fov_half) / (2.0 * P.fov_half) * np;
+            const double fv = (pv + P.fov_half) / (2.0 * P.fov_half) * np;
+            if (fu >= 0.0 && fu < np && fv >= 0.0 && fv < np) {
+              const int64_t iu = (int64_t)floor(fu), iv = (int64_t)floor(fv);
+              st_img = P.t.cam_image + P.cam[cam].img_off + (iv * np + iu) * P.cam_nb + b;
+            }
+          }
+          st_w = w;
+        }
+        ++nq;
+        if ((nq & 31) == 0) flush(32);
+      }
+    }
+    if (nq & 31) flush(nq & 31);
+    nq = 0;
+    __syncwarp();
+  }
+
+#pragma unroll
+  for (int i = 0; i < kNumLaunchCounters; ++i) {
+    const unsigned long long v = warp_sum_ull(lc[i]);
+    if (lane == 0 && v) atomicAdd(L.counters + i, v);
+  }
+}
+
+template <typename R>
+static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
+  constexpr int kWarps = 8;
+  const size_t smem = sizeof(PeelEv<R>) * 32 * kWarps;
+  auto kern = k_transport<R, kWarps>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  if (bps > 0 && bps < occ) occ = bps;
+  kern<<<sm_count * occ, kWarps * 32, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport(const LaunchDev* L, int precision, int blocks_per_sm, int sm_count, cudaStream_t s) {
+  if (precision == 0) return launch_t<double>(L, blocks_per_sm, sm_count, s);
+  return launch_t<float>(L, blocks_per_sm, sm_count, s);
+}
+
+}  // namespace colt
+
+namespace colt {
+int transport_grid_size(int precision, int blocks_per_sm, int sm_count) {
+  constexpr int kWarps = 8;
+  int occ = 0;
+  if (precision == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<double, kWarps>, kWarps * 32,
+                                                  sizeof(PeelEv<double>) * 32 * kWarps);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<float, kWarps>, kWarps * 32,
+                                                  sizeof(PeelEv<float>) * 32 * kWarps);
+  }
+  if (occ < 1) occ = 1;
+  if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+  return occ * sm_count;
+}
+}  // namespace colt

@@ -95,6 +95,7 @@ class RunSpec:
     cam_nbins: int = 200
     fov_half: float = 0.0           # 0 -> half of the box width
     precision: int = 1              # 0 plain FP64, 1 mixed (FP32 transport)
+    pid_offset: int = 0             # packets are ids pid_offset .. pid_offset + n_packets - 1
 
 
 def sigma0_recipe(T: float) -> float:

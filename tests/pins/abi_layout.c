@@ -1,0 +1,16 @@
+/* Prints sizeof / offsetof of the public ABI structs, for the binding test. */
+#include <stddef.h>
+#include <stdio.h>
+#include "colt.h"
+int main(void) {
+  printf("colt_grid_desc %zu\n", sizeof(colt_grid_desc));
+  printf("colt_camera %zu\n", sizeof(colt_camera));
+  printf("colt_run_params %zu\n", sizeof(colt_run_params));
+  printf("colt_result %zu\n", sizeof(colt_result));
+  printf("colt_stats %zu\n", sizeof(colt_stats));
+  printf("colt_scatter_io %zu\n", sizeof(colt_scatter_io));
+  printf("off_scatter_n_trials %zu\n", offsetof(colt_scatter_io, n_trials));
+  printf("off_run_precision %zu\n", offsetof(colt_run_params, precision));
+  printf("off_result_pk_freq %zu\n", offsetof(colt_result, pk_freq));
+  return 0;
+}

@@ -1,0 +1,97 @@
+"""Serving through the C ABI: colt_submit / colt_poll / colt_wait /
+colt_read_spectrum with continuous batching.  Each request's result in the mix
+equals its result alone (colt_run with the same grid and parameters):
+integer tallies bitwise, peel-off sums up to FP64 summation order.  Memory
+admission queues what does not fit and rejects what never can."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1409_4480_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    grids = [S.sphere(24, 1e4, 1e4, v_max_kms=100.0, tau_dust=0.5),
+             S.slab(16, 100.0, 1e5, v_max_kms=-50.0, tau_dust=0.2, nxy=4),
+             S.sphere(16, 10.0, 3e4)]
+    cams = S.axis_cameras(0)
+    reqs = []
+    for i, (gi, n) in enumerate([(0, 3000), (1, 20000), (2, 1000), (0, 50000), (1, 700), (2, 9000)]):
+        reqs.append((gi, S.RunSpec(n_packets=n, seed=4000 + i, albedo=0.32, spec_units=1, spec_lo=-400,
+                                   spec_hi=400, spec_nbins=80, cameras=cams if i % 2 == 0 else [],
+                                   cam_units=1, cam_lo=-400, cam_hi=400, cam_nbins=40)))
+    return grids, reqs
+
+
+def test_batched_equals_alone(colt):
+    ctx = colt.colt_init(0)
+    try:
+        grids, reqs = _mix()
+        hs = [colt.colt_create_grid(ctx, g) for g in grids]
+        alone = [colt.colt_run(ctx, hs[gi], sp) for gi, sp in reqs]
+        ids = []
+        for gi, sp in reqs:                      # arrivals while earlier work runs
+            ids.append(colt.colt_submit(ctx, hs[gi], sp))
+            colt.colt_poll(ctx, ids[-1])
+        for rid in ids:
+            colt.colt_wait(ctx, rid, timeout_ms=120000)
+        for rid, (gi, sp), ref in zip(ids, reqs, alone):
+            st = colt.colt_poll(ctx, rid)
+            assert st["done"] and st["packets_done"] == sp.n_packets and st["latency_ms"] > 0
+            got = colt.colt_read_result(ctx, rid, sp)
+            assert np.array_equal(got["spec"], ref["spec"])
+            for key in ("n_emitted", "n_escaped", "n_absorbed", "n_capped", "n_scat", "n_scat_hi"):
+                assert got[key] == ref[key], key
+            if sp.cameras:
+                assert np.allclose(got["cam_spec"], ref["cam_spec"], rtol=1e-9, atol=1e-300)
+                c0 = colt.colt_read_spectrum(ctx, rid, 0, sp.cam_nbins)
+                assert np.allclose(c0, ref["cam_spec"][0], rtol=1e-9, atol=1e-300)
+            esc = colt.colt_read_spectrum(ctx, rid, -1, sp.spec_nbins)
+            assert np.array_equal(esc, ref["spec"].astype(np.float64))
+            colt.colt_release(ctx, rid)
+        for h in hs:
+            colt.colt_destroy_grid(ctx, h)
+    finally:
+        colt.colt_finalize(ctx)
+
+
+def test_admission_by_memory(colt):
+    g = S.sphere(16, 1e4, 1e4)
+    grid_bytes = g.n_cells * 32
+    big = S.RunSpec(n_packets=2000, seed=1, spec_units=1, spec_lo=-400, spec_hi=400, spec_nbins=100,
+                    cameras=S.axis_cameras(64), cam_units=1, cam_lo=-400, cam_hi=400, cam_nbins=100)
+    img_bytes = 6 * 64 * 64 * 100 * 8
+    ctx = colt.colt_init(0, mem_budget_bytes=grid_bytes + int(1.5 * img_bytes) + (1 << 20))
+    try:
+        h = colt.colt_create_grid(ctx, g)
+        # images are not kept by serving requests; make requests heavy through bins
+        heavy = S.RunSpec(**{**big.__dict__, "cam_nbins": 40000, "cameras": S.axis_cameras(0)})
+        r1 = colt.colt_submit(ctx, h, heavy)
+        r2 = colt.colt_submit(ctx, h, S.RunSpec(**{**heavy.__dict__, "seed": 2}))
+        st2 = colt.colt_poll(ctx, r2)
+        colt.colt_wait(ctx, r1, timeout_ms=60000)
+        colt.colt_release(ctx, r1)               # frees memory -> r2 admitted
+        colt.colt_wait(ctx, r2, timeout_ms=60000)
+        assert colt.colt_poll(ctx, r2)["done"]
+        colt.colt_release(ctx, r2)
+        # a request that can never fit is refused at once
+        never = S.RunSpec(**{**heavy.__dict__, "cam_nbins": 4_000_000})
+        with pytest.raises(colt.ColtError) as e:
+            colt.colt_submit(ctx, h, never)
+        assert e.value.code == colt.COLT_ENOMEM
+        # reading a result before completion is EAGAIN
+        r3 = colt.colt_submit(ctx, h, S.RunSpec(n_packets=200000, seed=3, spec_lo=-40, spec_hi=40))
+        st = colt.colt_poll(ctx, r3)
+        if not st["done"]:
+            with pytest.raises(colt.ColtError) as e:
+                colt.colt_read_spectrum(ctx, r3, -1, 100)
+            assert e.value.code == colt.COLT_EAGAIN
+        colt.colt_wait(ctx, r3, timeout_ms=120000)
+        colt.colt_release(ctx, r3)
+        colt.colt_destroy_grid(ctx, h)
+        del st2
+    finally:
+        colt.colt_finalize(ctx)
