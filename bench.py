@@ -1,17 +1,23 @@
 """Benchmark of the Lyman-alpha packet transport on one (or N) GB300.
 
-Workload (the 128^3 expanding/contracting dusty sphere suite): a uniform
-128^3 sphere at T = 1e4 K, tau0 in {1e5, 1e6, 1e7}, Hubble-like velocity with
-v_max in {-200, 0, +200} km/s (nine cases), dust tau_d = 1 with albedo 0.32,
-peel-off to six axis cameras of 128^2 pixels x 200 bins over +-1000 km/s,
-1e6 packets per case for the whole job.  A step is one batch of packets of
-all nine cases in one persistent launch (colt_run_batch, mixed precision);
-the job is steps_per_job batches.  Inputs are synthetic (seeded generators).
+Workload (the 128^3 dusty-sphere suite): a uniform 128^3 sphere at T = 1e4 K,
+tau0 in {1e5, 1e6, 1e7}, Hubble-like velocity with v_max in {-200, 0, +200}
+km/s (nine cases), dust tau_d = 1 with albedo 0.32, peel-off to six axis
+cameras of 128^2 pixels x 200 bins over +-1000 km/s, 1e6 packets per case for
+the whole job.  A step is one batch of `--packets-per-case` packets of all nine
+cases (disjoint packet-id ranges per step and rank), mixed precision.
+Inputs are synthetic (seeded generators), resident in HBM before timing.
 
-value      scatterings/s (executed, core-skipped ones not counted), whole job
-e2e        the same metric through colt_solve with host fields: grid upload +
-           records + non-local a*tau + transport + result download per step
+value      scatterings/s (executed, core-skipped ones not counted) of the
+           served form: every step's nine solves are submitted to the
+           continuous-batching scheduler (colt_submit), which keeps several
+           persistent launches in flight; p50/p99 request latency beside it
+plain      the same steps through the blocking single-launch call
+           (colt_run_batch), one step
+e2e        one step through colt_create_grid (host fields) + colt_submit +
+           colt_read_result (spectra and image cubes back to the host)
 --impl reference   the FP64 CPU oracle on the host cores, bounded samples
+--single-case I    one blocking solve of case I (profiling driver)
 """
 import argparse
 import json
@@ -34,6 +40,7 @@ VMAX = (-200.0, 0.0, 200.0)
 PACKETS_PER_CASE_JOB = 10 ** 6
 METRIC = "scatterings/s & photons/s at oracle-matched spectra; served p50/p99 latency"
 UNIT = "scatterings/s"
+WORKLOAD = "sphere128_T1e4_dust1_9cases_6cam"
 
 
 def cases():
@@ -119,7 +126,7 @@ def oracle_sample(target_s=15.0, case=(1e6, 0.0), cores=0):
     g = case_grid(*case)
     i = cases().index(case)
     n = 16
-    O.run(g, case_spec(i, 4, 0, images=False), n_threads=cores)  # build + warm
+    O.run(g, case_spec(i, 4, 0, images=False), n_threads=cores)  # warm (page-in, grid derivation)
     while True:
         r = O.run(g, case_spec(i, n, 0, images=False), n_threads=cores)
         if r["seconds"] > target_s / 4 or n >= 1 << 20:
@@ -139,7 +146,6 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    steps_rates = []
     cores = os.cpu_count()
     t_all = 0.0
     n_scat = 0
@@ -153,21 +159,33 @@ def run_reference(args):
             t_all += r["seconds"]
             n_scat += r["n_scat"]
             n_pk += args.ref_packets
-            steps_rates.append(r["n_scat"] / r["seconds"])
     value = n_scat / t_all
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "photons_per_s": n_pk / t_all,
-            "config": {"workload": "sphere128_T1e4_dust1_9cases_6cam", "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200}",
+            "config": {"workload": WORKLOAD, "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200}",
                        "packets_per_step": args.ref_packets, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.ref_packets} packets per step, one case per step cycling through the 9"},
+                             "sample": f"{args.ref_packets} packets per step, one case per step cycling "
+                                       f"through the 9 (6-camera peel-off spectra, no images)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU leg --
+def run_single_case(args):
+    from paper_1409_4480_gb300 import colt as C
+    ctx = C.colt_init(0)
+    t, v = cases()[args.single_case]
+    h = C.colt_create_grid(ctx, case_grid(t, v))
+    r = C.colt_run(ctx, h, case_spec(args.single_case, args.packets_per_case, 0, images=not args.no_images))
+    print(json.dumps({"case": args.single_case, "packets": args.packets_per_case, "kernel_ms": r["kernel_ms"],
+                      "scatterings": r["n_scat"], "peel_visits": r["n_peel_visits"],
+                      "cell_visits": r["n_cell_visits"]}))
+    C.colt_finalize(ctx)
+
+
 def run_gpu(args):
     import torch
     from paper_1409_4480_gb300 import colt as C
@@ -184,42 +202,51 @@ def run_gpu(args):
     ctx = C.colt_init(local, 0, stream.cuda_stream)
     info = C.colt_device_info(ctx)
     B = args.packets_per_case
-    # grids resident in HBM before the timed region
+    img = not args.no_images
     grids_h = [case_grid(t, v) for t, v in cases()]
     hs = [C.colt_create_grid(ctx, g) for g in grids_h]
-    img = not args.no_images
 
-    def step(s):
-        # packet ids of this (step, rank): weak scaling, disjoint ranges
-        off = (s * world + rank) * B
-        specs = [case_spec(i, B, off, images=img) for i in range(9)]
-        return C.colt_run_batch(ctx, hs, specs, images=img, outputs=False)
+    def specs_of(s):
+        off = (s * world + rank) * B          # disjoint packet ids per (step, rank)
+        return [case_spec(i, B, off, images=img) for i in range(9)]
+
+    def submit(s):
+        return [(C.colt_submit(ctx, hs[i], sp), sp) for i, sp in enumerate(specs_of(s))]
+
+    def finish(reqs):
+        out = []
+        for rid, sp in reqs:
+            C.colt_wait(ctx, rid, -1.0)
+        for rid, sp in reqs:
+            st = C.colt_poll(ctx, rid)
+            res = C.colt_read_result(ctx, rid, S.RunSpec(**{**sp.__dict__, "cameras": []}))
+            out.append((st, res))
+            C.colt_release(ctx, rid)
+        return out
 
     for s in range(args.warmup):
-        step(s)
+        finish(submit(s))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = launch_count(C, ctx, hs[0])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tot_scat = tot_pk = 0
-    kms = []
-    visits = [0, 0, 0]
     with ClockSampler(local) as clk:
         ev0.record(stream)
         t0 = time.perf_counter()
+        reqs = []
         for s in range(args.warmup, args.warmup + args.steps):
-            res = step(s)
-            tot_scat += sum(r["n_scat"] for r in res)
-            tot_pk += sum(r["n_emitted"] for r in res)
-            kms.append(res[0]["kernel_ms"])
-            visits[0] += res[0]["n_cell_visits"]
-            visits[1] += res[0]["n_peel_visits"]
-            visits[2] += res[0]["n_peel_rays"]
+            reqs += submit(s)
+        done = finish(reqs)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     ms = ev0.elapsed_time(ev1)
+    launches = launch_count(C, ctx, hs[0]) - launches0
+    tot_scat = sum(r["n_scat"] for _, r in done)
+    tot_pk = sum(r["n_emitted"] for _, r in done)
+    lat = [st["latency_ms"] for st, _ in done]
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -230,58 +257,82 @@ def run_gpu(args):
     value = tot_scat / (ms / 1e3)
     photons = tot_pk / (ms / 1e3)
 
-    # end to end: host fields, colt_solve per case (upload, records, a*tau_NL,
-    # transport, download of spectra and image cubes), one step
+    # plain: the blocking single-launch call on one step (visit counts for the roofline)
+    s_plain = args.warmup + args.steps
+    tp0 = time.perf_counter()
+    res_plain = C.colt_run_batch(ctx, hs, specs_of(s_plain), images=img, outputs=False)
+    plain_wall = time.perf_counter() - tp0
+    plain_scat = sum(r["n_scat"] for r in res_plain)
+    plain_ms = res_plain[0]["kernel_ms"]
+    visits = (res_plain[0]["n_cell_visits"], res_plain[0]["n_peel_visits"], res_plain[0]["n_peel_rays"])
+
+    # end to end: host fields -> grids -> served solves -> results (spectra + images) on the host
     e2e = None
     if not args.no_e2e:
+        s_e2e = s_plain + 1
         h2d = d2h = 0
-        t0 = time.perf_counter()
-        e2e_scat = 0
         ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
         ev2.record(stream)
-        s = args.warmup + args.steps
-        for i, g in enumerate(grids_h):
-            sp = case_spec(i, B, (s * world + rank) * B, images=img)
-            r = C.colt_solve(ctx, g, sp, images=img)
+        ghs = [C.colt_create_grid(ctx, g) for g in grids_h]
+        h2d = sum(6 * 4 * g.n_cells for g in grids_h)
+        off = (s_e2e * world + rank) * B
+        sps = [case_spec(i, B, off, images=img) for i in range(9)]
+        rids = [C.colt_submit(ctx, ghs[i], sp) for i, sp in enumerate(sps)]
+        e2e_scat = 0
+        for rid, sp in zip(rids, sps):
+            C.colt_wait(ctx, rid, -1.0)
+        for rid, sp in zip(rids, sps):
+            r = C.colt_read_result(ctx, rid, sp) if not img else read_with_images(C, ctx, rid, sp)
             e2e_scat += r["n_scat"]
-            h2d += 6 * 4 * g.n_cells
-            d2h += r["spec"].nbytes + r["cam_spec"].nbytes + r["cam_spec2"].nbytes + (r["cam_image"].nbytes if img else 0)
+            d2h += sum(v.nbytes for k, v in r.items() if isinstance(v, np.ndarray))
+            C.colt_release(ctx, rid)
+        for gh in ghs:
+            C.colt_destroy_grid(ctx, gh)
         ev3.record(stream)
         torch.cuda.synchronize()
         e2e_ms = ev2.elapsed_time(ev3)
         e2e = {"value": e2e_scat / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "path": "colt_solve (host fields -> device records -> a*tau_NL -> transport -> host results)"}
+               "path": "colt_create_grid (host fields) -> colt_submit -> colt_wait -> colt_read_result "
+                       "(escape + camera spectra + image cubes) -> colt_destroy_grid"}
 
     # roofline of the transport kernel: FP32 issue-bound
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12
-    kern_ms = statistics.mean(kms)
-    ops = (args.flops_peel * visits[1] + args.flops_cell * visits[0] + args.flops_scat * tot_scat / world) / args.steps
-    achieved = ops / (kern_ms / 1e3) / 1e12
+    per_scat = ((args.flops_peel * visits[1] + args.flops_cell * visits[0]) / max(plain_scat, 1)) + args.flops_scat
+    achieved = per_scat * tot_scat / (ms / 1e3) / 1e12
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
         cpu["kind"] = "oracle"
+    lat_sorted = sorted(lat)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "photons_per_s": photons,
-            "config": {"workload": "sphere128_T1e4_dust1_9cases_6cam",
+            "served_latency_ms": {"p50": float(np.percentile(lat_sorted, 50)),
+                                  "p99": float(np.percentile(lat_sorted, 99)), "n_requests": len(lat),
+                                  "arrivals": "burst: all steps' requests submitted at t0"},
+            "plain": {"value": plain_scat / (plain_ms / 1e3), "unit": UNIT, "kernel_ms": plain_ms,
+                      "wall_s": plain_wall, "path": "colt_run_batch, one blocking launch of the 9 solves"},
+            "config": {"workload": WORKLOAD,
                        "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200} km/s, tau_d=1, A=0.32",
                        "packets_per_case_per_step": B, "steps_per_job": PACKETS_PER_CASE_JOB // B,
                        "cameras": "6 x 128^2 x 200" if img else "6 x 200 (no images)",
                        "grid": "128^3 Cartesian, 32 B records", "precision": "mixed (FP32 transport, FP64 tau/escape)",
-                       "launch": "colt_run_batch: one persistent launch of all 9 cases per step",
-                       "l2": "records 9 x 67 MB + tallies 9 x 157 MB > 129 MB L2: inputs larger than L2"},
-            "gpu_launches": args.steps,
-            "kernel_ms_mean": kern_ms,
-            "counts": {"scatterings": tot_scat, "packets": tot_pk, "cell_visits": visits[0],
-                       "peel_visits": visits[1], "peel_rays": visits[2]},
+                       "launch": "served: colt_submit of 9 solves per step, persistent launches in flight",
+                       "l2": "records 9 x 67 MB + tallies 9 x 157 MB per step > 129 MB L2: inputs larger than L2"},
+            "gpu_launches": launches,
+            "counts": {"scatterings": tot_scat, "packets": tot_pk,
+                       "plain_step": {"scatterings": plain_scat, "cell_visits": visits[0], "peel_visits": visits[1],
+                                      "peel_rays": visits[2]}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
-                         "peak_source": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz (max SM clock of measured)"},
+                         "flops_per_scattering": per_scat,
+                         "peak_source": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz "
+                                        f"(max SM clock, of measured)"},
             "clocks": clk.summary(), "wall_s": wall}
     if e2e:
         line["e2e"] = e2e
@@ -294,14 +345,32 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def launch_count(C, ctx, h):
+    """Transport launches issued so far, read through a zero-packet request
+    (it completes at once and launches nothing)."""
+    rid = C.colt_submit(ctx, h, S.RunSpec(n_packets=0, seed=0))
+    n = C.colt_poll(ctx, rid)["launches"]
+    C.colt_release(ctx, rid)
+    return n
+
+
+def read_with_images(C, ctx, rid, sp):
+    """colt_read_result with the image cubes requested as well."""
+    import ctypes
+    r, out = C._result_arrays(sp, False, True)
+    C._check(ctx, C.lib().colt_read_result(ctx, ctypes.c_uint64(rid), ctypes.byref(r)))
+    return C._unpack(r, out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="colt", choices=["colt", "reference"])
-    ap.add_argument("--packets-per-case", type=int, default=1 << 15)
+    ap.add_argument("--packets-per-case", type=int, default=125000)
     ap.add_argument("--ref-packets", type=int, default=64)
+    ap.add_argument("--single-case", type=int, default=-1)
     ap.add_argument("--no-images", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -313,6 +382,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.single_case >= 0:
+        run_single_case(args)
     else:
         run_gpu(args)
 

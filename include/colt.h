@@ -155,7 +155,9 @@ typedef struct {
  *   cam_image  [sum_c npix_c^2 * cam_nbins]       per camera [v][u][bin]
  *   pk_status  [n_packets] 1 escaped, 2 absorbed, 3 capped
  *   pk_nscat   [n_packets] executed scatterings of each packet
- *   pk_freq    [n_packets] escape frequency (spec_units) of escaped packets */
+ *   pk_freq    [n_packets] escape frequency (spec_units) of escaped packets;
+ *                          for packets stopped by max_scatter, the lab-frame
+ *                          frequency at that moment; 0 otherwise */
 typedef struct {
   uint64_t n_emitted, n_escaped, n_absorbed, n_capped;
   uint64_t n_scat, n_scat_hi;
@@ -199,6 +201,7 @@ typedef struct {
   int admitted;
   uint64_t packets_done, packets_total;
   double submit_to_done_ms; /* latency, valid when done                          */
+  uint64_t ctx_launches;    /* transport kernel launches this context has issued */
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);

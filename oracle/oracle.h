@@ -131,7 +131,8 @@ typedef struct {
   /* optional per-packet records (length n_packets), may be NULL */
   int32_t*  pk_status;      /* 1 escaped, 2 absorbed, 3 capped                 */
   uint64_t* pk_nscat;
-  double*   pk_freq;        /* escape spectral coordinate (escaped only)       */
+  double*   pk_freq;        /* escape spectral coordinate; for packets capped by
+                               max_scatter the lab frequency at the cap        */
   uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
 } o_params;
 

@@ -279,7 +279,14 @@ static void run_packet(worker* w, uint64_t idx) {
       for (int i = 0; i < 3; ++i) k[i] = s.k_f[i];
       x = s.x_f;
     }
-    if (nscat >= p->max_scatter) { status = 3; break; }
+    if (nscat >= p->max_scatter) {
+      /* capped by the scattering limit: report the lab-frame frequency the
+       * packet has at that moment */
+      double x_lab = x + dot3(k, &g->u[3 * c]);
+      s_esc = spectral_coord(p->spec_units, x_lab, g->vth[c], w->vth_ref);
+      status = 3;
+      break;
+    }
     tau = -log(B0[2]);
   }
   w->n_scat += nscat;
@@ -296,7 +303,7 @@ static void run_packet(worker* w, uint64_t idx) {
   }
   if (p->pk_status) p->pk_status[idx] = status;
   if (p->pk_nscat) p->pk_nscat[idx] = nscat;
-  if (p->pk_freq) p->pk_freq[idx] = (status == 1) ? s_esc : 0.0;
+  if (p->pk_freq) p->pk_freq[idx] = (status == 1 || status == 3) ? s_esc : 0.0;
 }
 
 #define CHUNK 16

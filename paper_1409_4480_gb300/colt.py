@@ -73,7 +73,8 @@ class Result(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("done", C.c_int), ("admitted", C.c_int), ("packets_done", C.c_uint64),
-                ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double)]
+                ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double),
+                ("ctx_launches", C.c_uint64)]
 
 
 class ScatterIO(C.Structure):
@@ -339,7 +340,7 @@ def colt_poll(ctx, req: int) -> dict:
     st = Stats()
     _check(ctx, lib().colt_poll(ctx, C.c_uint64(req), C.byref(done), C.byref(st)))
     return dict(done=bool(done.value), admitted=bool(st.admitted), packets_done=st.packets_done,
-                packets_total=st.packets_total, latency_ms=st.submit_to_done_ms)
+                packets_total=st.packets_total, latency_ms=st.submit_to_done_ms, launches=st.ctx_launches)
 
 
 def colt_wait(ctx, req: int, timeout_ms: float = -1.0):

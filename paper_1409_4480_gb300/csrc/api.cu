@@ -1,6 +1,14 @@
 // C ABI of libcolt (declared and documented in include/colt.h): contexts,
 // grids, blocking runs, the continuous-batching scheduler and the parity
 // helpers.  Host-side runtime in C++17; all compute is in the CUDA kernels.
+//
+// Launch slots: a persistent launch needs a header + job table in device
+// memory (staged from pinned host memory) and a work counter.  The context
+// owns kSlots of them, each with its own stream, so the serving scheduler can
+// keep several launches in flight: the GPU's block scheduler hands SMs freed
+// by one launch's finished CTAs to the next launch, so a launch's tail of
+// long histories overlaps new work.  Slot 0 runs on the context stream and
+// also serves the blocking calls.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,8 +28,9 @@ using namespace colt;
 
 namespace {
 
-constexpr int kMaxJobs = 256;            // requests per persistent launch
-constexpr uint64_t kStepPackets = 1ull << 18;  // packet budget of one serving step
+constexpr int kMaxJobs = 256;                  // solves per persistent launch
+constexpr int kSlots = 3;                      // launches in flight (serving)
+constexpr uint64_t kStepPackets = 1ull << 20;  // packet budget of one serving launch
 
 double now_ms() {
   using namespace std::chrono;
@@ -33,8 +42,6 @@ struct GridObj {
   float4* rec = nullptr;
   size_t bytes = 0;
 };
-
-struct Req;
 
 // Device + pinned staging for one persistent launch: header, job_end, jobs.
 struct LaunchBuf {
@@ -48,6 +55,16 @@ struct LaunchBuf {
   Job* jobs_h() { return reinterpret_cast<Job*>(host + 256 + 8 * kMaxJobs); }
   size_t off_end() const { return 256; }
   size_t off_jobs() const { return 256 + 8 * kMaxJobs; }
+};
+
+struct Slot {
+  LaunchBuf lb;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  std::vector<std::pair<uint64_t, uint64_t>> jobs;  // (request id, packets)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
 struct Tally {
@@ -71,11 +88,10 @@ struct Req {
   colt_grid grid = 0;
   colt_run_params p{};
   std::vector<colt_camera> cams;
-  RunDev run;                           // filled at admission (tally pointers)
+  RunDev run;                           // tally pointers filled at admission
   Tally tally;
   int state = kQueued;
   uint64_t next_local = 0;              // packets handed to launches
-  uint64_t in_flight = 0;               // packets of the launch in flight
   uint64_t done_packets = 0;
   double t_submit = 0, t_done = 0;
   size_t need_bytes = 0;
@@ -98,12 +114,9 @@ struct colt_ctx {
   std::map<uint64_t, GridObj> grids;
   std::map<uint64_t, std::unique_ptr<Req>> reqs;
   std::deque<uint64_t> queue;           // queued request ids (FIFO)
-  LaunchBuf lb;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_step = nullptr;
-  // serving
-  bool step_in_flight = false;
-  std::vector<std::pair<uint64_t, uint64_t>> step_jobs;  // (req id, packets)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  Slot slots[kSlots];
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_alloc = nullptr;
+  uint64_t launches = 0;                // transport kernel launches issued
 };
 
 namespace {
@@ -117,9 +130,9 @@ int cuda_fail(colt_ctx* c, cudaError_t e, const char* where) {
   return fail(c, COLT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define CU(call)                                         \
-  do {                                                   \
-    cudaError_t e_ = (call);                             \
+#define CU(call)                                             \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
@@ -139,7 +152,7 @@ int camera_axis(const double d[3], int* axis, int* sgn) {
   return 0;
 }
 
-int validate_params(colt_ctx* ctx, const GridObj& g, const colt_run_params* p) {
+int validate_params(colt_ctx* ctx, const colt_run_params* p) {
   if (!p) return fail(ctx, COLT_EINVAL, "params is NULL");
   if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo)) return fail(ctx, COLT_EINVAL, "bad escape-spectrum bins");
   if (p->n_cam < 0 || p->n_cam > kMaxCams) return fail(ctx, COLT_EINVAL, "n_cam must be in [0, 8]");
@@ -157,12 +170,11 @@ int validate_params(colt_ctx* ctx, const GridObj& g, const colt_run_params* p) {
   if (p->spec_units != COLT_UNITS_X && p->spec_units != COLT_UNITS_DV_KMS) return fail(ctx, COLT_EINVAL, "bad spec_units");
   if (p->n_cam > 0 && p->cam_units != COLT_UNITS_X && p->cam_units != COLT_UNITS_DV_KMS)
     return fail(ctx, COLT_EINVAL, "bad cam_units");
-  if ((p->spec_units == COLT_UNITS_X || p->cam_units == COLT_UNITS_X) && !(p->T_ref > 0))
+  if ((p->spec_units == COLT_UNITS_X || (p->n_cam > 0 && p->cam_units == COLT_UNITS_X)) && !(p->T_ref > 0))
     return fail(ctx, COLT_EINVAL, "T_ref must be > 0 for x units");
   if (!(p->tau_esc_max > 0)) return fail(ctx, COLT_EINVAL, "tau_esc_max must be > 0");
   if (!(p->albedo >= 0 && p->albedo <= 1)) return fail(ctx, COLT_EINVAL, "albedo must be in [0,1]");
   if (!(p->src_sigma >= 0)) return fail(ctx, COLT_EINVAL, "src_sigma must be >= 0");
-  (void)g;
   return COLT_OK;
 }
 
@@ -182,7 +194,7 @@ size_t tally_bytes(const colt_run_params* p, bool per_packet) {
   return b;
 }
 
-// Allocate and zero one request's tallies on the context stream.
+// Allocate and zero one solve's tallies (stream-ordered pool on the context stream).
 int alloc_tally(colt_ctx* ctx, const colt_run_params* p, bool per_packet, Tally* t) {
   t->bytes = tally_bytes(p, per_packet) + 256;
   t->stream = ctx->stream;
@@ -208,7 +220,6 @@ int alloc_tally(colt_ctx* ctx, const colt_run_params* p, bool per_packet, Tally*
     t->pk_nscat = reinterpret_cast<uint64_t*>(take(sizeof(uint64_t) * p->n_packets));
     t->pk_freq = reinterpret_cast<double*>(take(sizeof(double) * p->n_packets));
   }
-  // the carve-up adds at most 255 bytes of padding per array
   return COLT_OK;
 }
 
@@ -217,7 +228,7 @@ void free_tally(Tally* t) {
   *t = Tally{};
 }
 
-// Job description from a grid and parameters (tally pointers filled later).
+// Job description from a grid and parameters (tally pointers attached later).
 RunDev make_run(const GridObj& g, const colt_run_params* p) {
   RunDev r;
   r.n_packets = p->n_packets;
@@ -254,6 +265,8 @@ RunDev make_run(const GridObj& g, const colt_run_params* p) {
     fov = std::max(fov, 0.5 * (g.dev.hi[a] - g.dev.lo[a]));
   }
   r.fov_half = p->fov_half > 0 ? p->fov_half : fov;
+  r.pix_scale = 0.5 / r.fov_half;
+  r.cam_inv_width = p->cam_hi > p->cam_lo ? (double)r.cam_nb / (p->cam_hi - p->cam_lo) : 1.0;
   return r;
 }
 
@@ -268,9 +281,17 @@ void attach_tally(RunDev* r, const Tally& t) {
   r->t.pk_freq = t.pk_freq;
 }
 
-int ensure_launch_buf(colt_ctx* ctx) {
-  LaunchBuf& lb = ctx->lb;
+int ensure_slot(colt_ctx* ctx, int si) {
+  Slot& sl = ctx->slots[si];
+  LaunchBuf& lb = sl.lb;
   if (lb.host) return COLT_OK;
+  if (si == 0) {
+    sl.stream = ctx->stream;
+  } else {
+    CU(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+    sl.own_stream = true;
+  }
+  CU(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
   lb.bytes = lb.off_jobs() + sizeof(Job) * kMaxJobs;
   CU(cudaMallocHost(&lb.host, lb.bytes));
   CU(cudaMalloc(&lb.dev, lb.bytes));
@@ -287,50 +308,54 @@ int ensure_launch_buf(colt_ctx* ctx) {
   return COLT_OK;
 }
 
-// Enqueue one persistent launch over the jobs staged in lb.host:
-// header/job table copy, counter reset, kernel.  Recorded once per precision
-// as a CUDA graph and replayed.
-int enqueue_launch(colt_ctx* ctx, int precision, int blocks_per_sm) {
-  LaunchBuf& lb = ctx->lb;
+// Enqueue one persistent launch over the jobs staged in the slot's host
+// buffer: header/job-table copy, counter reset, kernel.  Recorded once per
+// (slot, precision) as a CUDA graph and replayed.
+int enqueue_launch(colt_ctx* ctx, int si, int precision, int blocks_per_sm) {
+  Slot& sl = ctx->slots[si];
+  LaunchBuf& lb = sl.lb;
   const int gi = precision == COLT_PLAIN ? 0 : 1;
+  ++ctx->launches;
   if (blocks_per_sm > 0) {
-    CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, ctx->stream));
+    CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
+    CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, sl.stream));
     CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, blocks_per_sm, ctx->sm_count,
-                        ctx->stream));
+                        sl.stream));
     return COLT_OK;
   }
-  if (!ctx->graph[gi]) {
+  if (!sl.graph[gi]) {
     cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, ctx->stream);
-    cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, ctx->stream);
+    CU(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
+    cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, sl.stream);
     cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, 0, ctx->sm_count,
-                                      ctx->stream);
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+                                      sl.stream);
+    cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "transport launch (capture)");
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-    cudaError_t ie = cudaGraphInstantiate(&ctx->graph[gi], g, 0);
+    cudaError_t ie = cudaGraphInstantiate(&sl.graph[gi], g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
   }
-  CU(cudaGraphLaunch(ctx->graph[gi], ctx->stream));
+  CU(cudaGraphLaunch(sl.graph[gi], sl.stream));
   return COLT_OK;
 }
 
-int check_device_error(colt_ctx* ctx) {
+// After the slot's launch completed: device-side error flag.
+int check_device_error(colt_ctx* ctx, int si) {
+  Slot& sl = ctx->slots[si];
   int h = 0;
-  if (!ctx->lb.error) return COLT_OK;
-  CU(cudaMemcpyAsync(&h, ctx->lb.error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
+  if (!sl.lb.error) return COLT_OK;
+  CU(cudaMemcpyAsync(&h, sl.lb.error, sizeof(int), cudaMemcpyDeviceToHost, sl.stream));
+  CU(cudaStreamSynchronize(sl.stream));
   if (h) {
-    CU(cudaMemsetAsync(ctx->lb.error, 0, sizeof(int), ctx->stream));
+    CU(cudaMemsetAsync(sl.lb.error, 0, sizeof(int), sl.stream));
     return fail(ctx, COLT_EDEVICE, "transport kernel raised its error flag (cell index out of range)");
   }
   return COLT_OK;
 }
 
-// Copy a request's tallies into a caller's colt_result.
+// Copy a solve's tallies into a caller's colt_result.
 int copy_result(colt_ctx* ctx, const colt_run_params* p, const Tally& t, colt_result* out, bool per_packet) {
   unsigned long long cnt[kNumCounters];
   CU(cudaMemcpyAsync(cnt, t.counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
@@ -382,12 +407,13 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
     if (!src[i]) { f[i] = nullptr; continue; }
     if (d->fields_mem == COLT_MEM_DEVICE) {
       hf[i].resize(n);
-      CU(cudaMemcpy(hf[i].data(), src[i], sizeof(float) * n, cudaMemcpyDeviceToHost));
+      CU(cudaMemcpyAsync(hf[i].data(), src[i], sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
       f[i] = hf[i].data();
     } else {
       f[i] = src[i];
     }
   }
+  CU(cudaStreamSynchronize(ctx->stream));
   const size_t bytes = sizeof(float4) * 2 * (size_t)n;
   if (ctx->used + bytes > ctx->budget) return fail(ctx, COLT_ENOMEM, "grid exceeds the memory budget");
   std::vector<float4> rec(2 * (size_t)n);
@@ -417,11 +443,11 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
   G.rec = g->rec;
   // non-local a tau (Eq. atauNL), once per grid
   float* dn = nullptr;
-  CU(cudaMalloc(&dn, sizeof(float) * n));
+  CU(cudaMallocAsync(&dn, sizeof(float) * n, ctx->stream));
   CU(cudaMemcpyAsync(dn, f[0], sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
   cudaError_t e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->stream);
+  cudaFreeAsync(dn, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
-  cudaFree(dn);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "atau_nl kernel");
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "atau_nl sync");
   g->bytes = bytes;
@@ -429,23 +455,34 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
 }
 
 // ----------------------------------------------------------- serving core --
-int serve_complete_step(colt_ctx* ctx) {
-  // called once the in-flight step has finished on the device
-  ctx->step_in_flight = false;
+// A slot's launch finished: account its packets to its requests.
+int complete_slot(colt_ctx* ctx, int si) {
+  Slot& sl = ctx->slots[si];
+  sl.in_flight = false;
   const double t = now_ms();
-  for (auto& jp : ctx->step_jobs) {
+  for (auto& jp : sl.jobs) {
     auto it = ctx->reqs.find(jp.first);
     if (it == ctx->reqs.end()) continue;
     Req& r = *it->second;
     r.done_packets += jp.second;
-    r.in_flight = 0;
     if (r.done_packets >= r.p.n_packets && r.state == kAdmitted) {
       r.state = kDone;
       r.t_done = t;
     }
   }
-  ctx->step_jobs.clear();
-  return check_device_error(ctx);
+  sl.jobs.clear();
+  return check_device_error(ctx, si);
+}
+
+// Wait for every in-flight launch (used before blocking calls).
+int drain_slots(colt_ctx* ctx) {
+  for (int si = 0; si < kSlots; ++si) {
+    if (!ctx->slots[si].in_flight) continue;
+    CU(cudaEventSynchronize(ctx->slots[si].done));
+    int rc = complete_slot(ctx, si);
+    if (rc) return rc;
+  }
+  return COLT_OK;
 }
 
 int serve_admit(colt_ctx* ctx) {
@@ -453,7 +490,7 @@ int serve_admit(colt_ctx* ctx) {
   while (!ctx->queue.empty()) {
     int active = 0;
     for (auto& kv : ctx->reqs) active += kv.second->state == kAdmitted;
-    if (active >= kMaxJobs) break;
+    if (active >= kMaxJobs * kSlots) break;
     const uint64_t id = ctx->queue.front();
     auto it = ctx->reqs.find(id);
     if (it == ctx->reqs.end()) { ctx->queue.pop_front(); continue; }
@@ -467,33 +504,37 @@ int serve_admit(colt_ctx* ctx) {
     ctx->queue.pop_front();
     ++admitted;
   }
+  if (admitted) CU(cudaEventRecord(ctx->ev_alloc, ctx->stream));
   return admitted;
 }
 
-// Build and enqueue one batched step over admitted requests (oldest first),
-// sharing a packet budget; all jobs of a step share one precision.
-int serve_launch_step(colt_ctx* ctx) {
+// Build and enqueue one batched launch on a free slot over admitted requests
+// with packets not yet handed out (oldest first), sharing a packet budget;
+// all jobs of a launch share one precision.  Returns 1 if launched.
+int serve_launch(colt_ctx* ctx, int si) {
   std::vector<Req*> act;
   for (auto& kv : ctx->reqs)
-    if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->p.n_packets) act.push_back(kv.second.get());
+    if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->p.n_packets)
+      act.push_back(kv.second.get());
   if (act.empty()) return 0;
   std::sort(act.begin(), act.end(), [](Req* a, Req* b) { return a->id < b->id; });
   const int prec = act.front()->p.precision;
   std::vector<Req*> sel;
   for (Req* r : act)
     if (r->p.precision == prec && (int)sel.size() < kMaxJobs) sel.push_back(r);
-  // fair share of the step budget, at least 1 packet each
-  uint64_t left = kStepPackets;
-  const uint64_t share = std::max<uint64_t>(1, kStepPackets / sel.size());
-  LaunchBuf& lb = ctx->lb;
-  int rc = ensure_launch_buf(ctx);
+  int rc = ensure_slot(ctx, si);
   if (rc) return rc;
+  Slot& sl = ctx->slots[si];
+  LaunchBuf& lb = sl.lb;
+  uint64_t left = kStepPackets;
   unsigned long long total = 0;
   int nj = 0;
-  ctx->step_jobs.clear();
-  for (Req* r : sel) {
+  sl.jobs.clear();
+  for (size_t i = 0; i < sel.size() && left > 0; ++i) {
+    Req* r = sel[i];
     const uint64_t rem = r->p.n_packets - r->next_local;
-    uint64_t take = std::min<uint64_t>(rem, std::max<uint64_t>(share, left / std::max<size_t>(1, sel.size() - nj)));
+    const uint64_t fair = std::max<uint64_t>(1, left / (sel.size() - i));
+    const uint64_t take = std::min<uint64_t>(rem, std::max<uint64_t>(fair, std::min<uint64_t>(rem, left)));
     if (take == 0) continue;
     const GridObj& g = ctx->grids.at(r->grid);
     Job& J = lb.jobs_h()[nj];
@@ -504,34 +545,43 @@ int serve_launch_step(colt_ctx* ctx) {
     total += take;
     lb.end_h()[nj] = total;
     r->next_local += take;
-    r->in_flight = take;
-    ctx->step_jobs.push_back({r->id, take});
+    sl.jobs.push_back({r->id, take});
     left = left > take ? left - take : 0;
     ++nj;
   }
+  if (nj == 0) return 0;
   LaunchDev* h = lb.hdr_h();
   h->n_jobs = nj;
   h->total = total;
-  rc = enqueue_launch(ctx, prec, 0);
+  // tallies were allocated and zeroed on the context stream
+  CU(cudaStreamWaitEvent(sl.stream, ctx->ev_alloc, 0));
+  rc = enqueue_launch(ctx, si, prec, 0);
   if (rc) return rc;
-  CU(cudaEventRecord(ctx->ev_step, ctx->stream));
-  ctx->step_in_flight = true;
+  CU(cudaEventRecord(sl.done, sl.stream));
+  sl.in_flight = true;
   return 1;
 }
 
 // Advance the scheduler without blocking on the device.
 int serve_pump(colt_ctx* ctx) {
-  if (ctx->step_in_flight) {
-    cudaError_t q = cudaEventQuery(ctx->ev_step);
-    if (q == cudaErrorNotReady) return COLT_OK;
-    if (q != cudaSuccess) return cuda_fail(ctx, q, "serving step");
-    int rc = serve_complete_step(ctx);
+  for (int si = 0; si < kSlots; ++si) {
+    Slot& sl = ctx->slots[si];
+    if (!sl.in_flight) continue;
+    cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return cuda_fail(ctx, q, "serving launch");
+    int rc = complete_slot(ctx, si);
     if (rc) return rc;
   }
   int rc = serve_admit(ctx);
   if (rc < 0) return rc;
-  rc = serve_launch_step(ctx);
-  return rc < 0 ? rc : COLT_OK;
+  for (int si = 0; si < kSlots; ++si) {
+    if (ctx->slots[si].in_flight) continue;
+    rc = serve_launch(ctx, si);
+    if (rc < 0) return rc;
+    if (rc == 0) break;
+  }
+  return COLT_OK;
 }
 
 }  // namespace
@@ -570,7 +620,7 @@ int colt_init(colt_ctx** out, int device, size_t mem_budget_bytes, void* cuda_st
   }
   cudaEventCreate(&ctx->ev0);
   cudaEventCreate(&ctx->ev1);
-  cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ctx->ev_alloc, cudaEventDisableTiming);
   *out = ctx;
   return COLT_OK;
 }
@@ -580,17 +630,24 @@ void colt_finalize(colt_ctx* ctx) {
   {
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
+    for (auto& sl : ctx->slots)
+      if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->reqs) free_tally(&kv.second->tally);
     for (auto& kv : ctx->grids) cudaFree(kv.second.rec);
-    for (auto& g : ctx->graph) if (g) cudaGraphExecDestroy(g);
-    if (ctx->lb.host) cudaFreeHost(ctx->lb.host);
-    if (ctx->lb.dev) cudaFree(ctx->lb.dev);
-    if (ctx->lb.work) cudaFree(ctx->lb.work);
-    if (ctx->lb.error) cudaFree(ctx->lb.error);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& sl : ctx->slots) {
+      for (auto& g : sl.graph) if (g) cudaGraphExecDestroy(g);
+      if (sl.lb.host) cudaFreeHost(sl.lb.host);
+      if (sl.lb.dev) cudaFree(sl.lb.dev);
+      if (sl.lb.work) cudaFree(sl.lb.work);
+      if (sl.lb.error) cudaFree(sl.lb.error);
+      if (sl.done) cudaEventDestroy(sl.done);
+      if (sl.own_stream) cudaStreamDestroy(sl.stream);
+    }
     cudaEventDestroy(ctx->ev0);
     cudaEventDestroy(ctx->ev1);
-    cudaEventDestroy(ctx->ev_step);
+    cudaEventDestroy(ctx->ev_alloc);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
@@ -661,16 +718,13 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     auto it = ctx->grids.find(grids[i]);
     if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
     gs[i] = &it->second;
-    int rc = validate_params(ctx, it->second, &params[i]);
+    int rc = validate_params(ctx, &params[i]);
     if (rc) return rc;
     if (params[i].precision != prec) return fail(ctx, COLT_EINVAL, "all solves of a batch need one precision");
   }
-  // a blocking run waits for any in-flight serving step first
-  if (ctx->step_in_flight) {
-    CU(cudaEventSynchronize(ctx->ev_step));
-    int rc = serve_complete_step(ctx);
-    if (rc) return rc;
-  }
+  // a blocking run waits for in-flight serving launches first
+  int rc = drain_slots(ctx);
+  if (rc) return rc;
   std::vector<bool> per_packet(n);
   size_t need = 0;
   for (int i = 0; i < n; ++i) {
@@ -680,9 +734,9 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   if (ctx->used + need > ctx->budget) return fail(ctx, COLT_ENOMEM, "tallies exceed the memory budget");
   std::vector<Tally> ts(n);
   auto free_all = [&]() { for (auto& t : ts) free_tally(&t); };
-  int rc = ensure_launch_buf(ctx);
+  rc = ensure_slot(ctx, 0);
   if (rc) return rc;
-  LaunchBuf& lb = ctx->lb;
+  LaunchBuf& lb = ctx->slots[0].lb;
   unsigned long long total = 0;
   for (int i = 0; i < n; ++i) {
     rc = alloc_tally(ctx, &params[i], per_packet[i], &ts[i]);
@@ -701,7 +755,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   float ms = 0;
   if (total > 0) {
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
-    rc = enqueue_launch(ctx, prec, params[0].blocks_per_sm);
+    rc = enqueue_launch(ctx, 0, prec, params[0].blocks_per_sm);
     if (rc) { free_all(); return rc; }
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     CU(cudaMemcpyAsync(lcnt, lb.work + 1, sizeof(lcnt), cudaMemcpyDeviceToHost, ctx->stream));
@@ -709,7 +763,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     if (se != cudaSuccess) { free_all(); return cuda_fail(ctx, se, "transport kernel"); }
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   }
-  rc = check_device_error(ctx);
+  rc = check_device_error(ctx, 0);
   for (int i = 0; i < n && !rc; ++i) {
     rc = copy_result(ctx, &params[i], ts[i], &out[i], per_packet[i]);
     out[i].kernel_ms = ms;
@@ -743,7 +797,7 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   cudaSetDevice(ctx->device);
   auto it = ctx->grids.find(grid);
   if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
-  int rc = validate_params(ctx, it->second, p);
+  int rc = validate_params(ctx, p);
   if (rc) return rc;
   if (ctx->queue.size() >= 4096) return fail(ctx, COLT_EAGAIN, "request queue full");
   auto r = std::make_unique<Req>();
@@ -752,15 +806,19 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   r->p = *p;
   r->cams.assign(p->cams, p->cams + p->n_cam);
   r->p.cams = r->cams.data();
-  r->need_bytes = tally_bytes(&r->p, false);
+  r->need_bytes = tally_bytes(&r->p, false) + 256;
   size_t grids_bytes = 0;
   for (auto& kv : ctx->grids) grids_bytes += kv.second.bytes;
   if (grids_bytes + r->need_bytes > ctx->budget)
     return fail(ctx, COLT_ENOMEM, "request can never fit in the memory budget");
   r->run = make_run(it->second, &r->p);
   r->t_submit = now_ms();
-  if (r->p.n_packets == 0) { r->state = kDone; r->t_done = r->t_submit; }
-  else ctx->queue.push_back(r->id);
+  if (r->p.n_packets == 0) {
+    r->state = kDone;
+    r->t_done = r->t_submit;
+  } else {
+    ctx->queue.push_back(r->id);
+  }
   *out = r->id;
   ctx->reqs[r->id] = std::move(r);
   return serve_pump(ctx);
@@ -782,6 +840,7 @@ int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
     st->packets_done = r.done_packets;
     st->packets_total = r.p.n_packets;
     st->submit_to_done_ms = r.state == kDone ? r.t_done - r.t_submit : 0.0;
+    st->ctx_launches = ctx->launches;
   }
   return COLT_OK;
 }
@@ -790,16 +849,19 @@ int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms) {
   if (!ctx) return COLT_EINVAL;
   const double t0 = now_ms();
   for (;;) {
-    int done = 0;
     {
       std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+      int done = 0;
       int rc = colt_poll(ctx, req, &done, nullptr);
       if (rc) return rc;
       if (done) return COLT_OK;
-      if (ctx->step_in_flight) {
-        // block on the in-flight step (bounded: one batched launch)
-        cudaError_t e = cudaEventSynchronize(ctx->ev_step);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "serving step");
+      // block on the oldest in-flight launch (bounded: one persistent launch)
+      int si = -1;
+      for (int k = 0; k < kSlots; ++k)
+        if (ctx->slots[k].in_flight) { si = k; break; }
+      if (si >= 0) {
+        cudaError_t e = cudaEventSynchronize(ctx->slots[si].done);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "serving launch");
       }
     }
     if (timeout_ms >= 0 && now_ms() - t0 > timeout_ms) return fail(ctx, COLT_ETIMEOUT, "colt_wait timed out");
@@ -814,10 +876,12 @@ int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out) {
   Req& r = *it->second;
   if (r.state != kDone) return fail(ctx, COLT_EAGAIN, "request not done");
   if (!r.tally.block) {  // zero-packet request
-    colt_result z{};
-    z.spec = out->spec;
-    if (out->spec) std::memset(out->spec, 0, sizeof(uint64_t) * r.p.spec_nbins);
-    *out = z;
+    uint64_t* spec = out->spec;
+    *out = colt_result{};
+    if (spec) {
+      std::memset(spec, 0, sizeof(uint64_t) * r.p.spec_nbins);
+      out->spec = spec;
+    }
     return COLT_OK;
   }
   out->pk_status = nullptr;
@@ -866,7 +930,6 @@ int colt_release(colt_ctx* ctx, colt_req req) {
     ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), req), ctx->queue.end());
   }
   if (r.tally.block) {
-    cudaStreamSynchronize(ctx->stream);
     ctx->used -= r.tally.bytes;
     free_tally(&r.tally);
   }
@@ -886,17 +949,17 @@ int colt_voigt(colt_ctx* ctx, const void* a, const void* x, void* H, size_t n, i
     return COLT_OK;
   }
   void *da = nullptr, *dx = nullptr, *dh = nullptr;
-  CU(cudaMalloc(&da, es * n + 1));
-  CU(cudaMalloc(&dx, es * n + 1));
-  CU(cudaMalloc(&dh, es * n + 1));
+  CU(cudaMallocAsync(&da, es * n + 1, ctx->stream));
+  CU(cudaMallocAsync(&dx, es * n + 1, ctx->stream));
+  CU(cudaMallocAsync(&dh, es * n + 1, ctx->stream));
   cudaMemcpyAsync(da, a, es * n, cudaMemcpyHostToDevice, ctx->stream);
   cudaMemcpyAsync(dx, x, es * n, cudaMemcpyHostToDevice, ctx->stream);
   cudaError_t e = launch_voigt(da, dx, dh, n, precision, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(H, dh, es * n, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(da, ctx->stream);
+  cudaFreeAsync(dx, ctx->stream);
+  cudaFreeAsync(dh, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
-  cudaFree(da);
-  cudaFree(dx);
-  cudaFree(dh);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "voigt kernel");
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "voigt sync");
   return COLT_OK;
@@ -909,12 +972,12 @@ int colt_scatter(colt_ctx* ctx, colt_scatter_io* io, size_t n, uint64_t seed, in
   cudaSetDevice(ctx->device);
   if (n == 0) return COLT_OK;
   void* d = nullptr;
-  CU(cudaMalloc(&d, sizeof(colt_scatter_io) * n));
+  CU(cudaMallocAsync(&d, sizeof(colt_scatter_io) * n, ctx->stream));
   cudaMemcpyAsync(d, io, sizeof(colt_scatter_io) * n, cudaMemcpyHostToDevice, ctx->stream);
   cudaError_t e = launch_scatter(d, n, seed, precision, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(io, d, sizeof(colt_scatter_io) * n, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(d, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
-  cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scatter kernel");
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "scatter sync");
   return COLT_OK;

@@ -166,9 +166,13 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
       if (q.v[1] < m_exp(-u * u)) { *n_trials = t; break; }
     }
   } else {
-    const R u0 = (xa < xcw) ? xa - R(1) / (xa + m_exp(R(1) - xa * xa) / a)
-                            : xcw - R(1) / xcw + R(0.15) * (xa - xcw);
-    const R alpha = m_atan2(a, xa - u0);
+    // d = |x| - u0 taken straight from the two u0 forms (u0_core = x - 1/(x +
+    // e^{1-x^2}/a), u0_wing = x_cw - 1/x_cw + 0.15 (x - x_cw)): forming it as
+    // |x| - u0 would cancel (d ~ a near |x| = 1) and cost FP32 its accuracy
+    const R d = (xa < xcw) ? R(1) / (xa + m_exp(R(1) - xa * xa) / a)
+                           : R(0.85) * (xa - xcw) + R(1) / xcw;
+    const R u0 = xa - d;
+    const R alpha = m_atan2(a, d);
     const R e0 = m_exp(-u0 * u0);
     const R p = alpha / ((R(1) - e0) * alpha + e0 * R(kPi));
     int t = 0;
@@ -180,8 +184,10 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
       const R psi = upper ? m_fma(R(kPi) - alpha, q.v[1], alpha) : alpha * q.v[1];
       R s, c;
       m_sincos(psi, &s, &c);
-      u = xa - a * c / s;
-      const R acc = upper ? m_exp((u0 - u) * (u0 + u)) : m_exp(-u * u);
+      const R tt = a * c / s;          // |x| - u
+      u = xa - tt;
+      // upper piece: exp(u0^2 - u^2) with u0 - u = tt - d, u0 + u = 2|x| - d - tt
+      const R acc = upper ? m_exp((tt - d) * (R(2) * xa - d - tt)) : m_exp(-u * u);
       if (q.v[2] < acc) { *n_trials = t; break; }
     }
   }

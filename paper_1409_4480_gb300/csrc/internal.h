@@ -72,8 +72,10 @@ struct RunDev {
   CamDev cam[kMaxCams];
   double cam_scale = 1.0;
   double cam_lo = 0, cam_hi = 1;
+  double cam_inv_width = 1.0;  // cam_nb / (cam_hi - cam_lo)
   int cam_nb = 1;
   double fov_half = 1.0;
+  double pix_scale = 0.5;      // 1 / (2 fov_half)
   double centre[3] = {0, 0, 0};
   Tallies t;
 };

@@ -29,12 +29,15 @@ namespace colt {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kMaxFlightVisits = 1u << 24;
+// peel-off cells a lane marches on its own (after the event cell) before the
+// warp takes the ray over
+constexpr int kLanePeel = 3;
 // recoil parameter over damping parameter: 2.536e-4 / 4.702e-4 (Sec. 2, Eq. recoil)
 constexpr double kGoverA = 2.536e-4 / 4.702e-4;
 
 template <typename R>
 struct PeelEv {
-  double pos[3];
+  R rel[3];     // event position relative to the box centre (cm), for image pixels
   int64_t cell;
   int ijk[3];
   int job;
@@ -44,12 +47,21 @@ struct PeelEv {
   R ua[3];      // atom velocity (HI scattering)
   R upar, g, RQ;
   R inv_vth, u[3];
+  R kHI, a, kd; // the event cell's opacity record (first cell of every peel-off ray)
   int type;     // 0: isotropic with W = 1 and x unchanged (emission, dust); 1: HI
 };
 
 __device__ __forceinline__ int bin_of(double s, double lo, double hi, int nb) {
   if (!(s >= lo) || !(s < hi)) return -1;
   int b = (int)floor((s - lo) * (double)nb / (hi - lo));
+  return (b >= 0 && b < nb) ? b : -1;
+}
+
+// bin of a peel-off frequency, in the transport precision
+template <typename R>
+__device__ __forceinline__ int bin_of_r(R s, R lo, R hi, R inv_width, int nb) {
+  if (!(s >= lo) || !(s < hi)) return -1;
+  const int b = (int)floor((s - lo) * inv_width);
   return (b >= 0 && b < nb) ? b : -1;
 }
 
@@ -85,21 +97,23 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   R x = 0;
   double tau = 0;
 
-  // staged peel-off tallies
-  double* st_spec = nullptr;
-  double* st_spec2 = nullptr;
-  double* st_img = nullptr;
-  double st_w = 0;
-  int nq = 0;
-
-  auto flush = [&](int upto) {
-    if (lane < upto && st_spec) {
-      atomicAdd(st_spec, st_w);
-      atomicAdd(st_spec2, st_w * st_w);
-      if (st_img) atomicAdd(st_img, st_w);
+  // one peel-off contribution W exp(-tau_esc) into the camera spectrum (and
+  // its square) and, inside the field of view, the image cube (Eq. SB)
+  auto peel_tally = [&](const RunDev& P, const PeelEv<R>& e, int cam, int ax, int s, int bin, double w) {
+    const int64_t si = (int64_t)cam * P.cam_nb + bin;
+    atomicAdd(P.t.cam_spec + si, w);
+    atomicAdd(P.t.cam_spec2 + si, w * w);
+    const int np = P.cam[cam].npix;
+    if (np > 0 && P.t.cam_image) {
+      const int au = (ax + 1) % 3, av = (ax + 2) % 3;
+      const R pix = R(P.pix_scale) * R(np);         // pixels per cm
+      const R fu = (R(s) * e.rel[au] + R(P.fov_half)) * pix;
+      const R fv = (e.rel[av] + R(P.fov_half)) * pix;
+      if (fu >= R(0) && fu < R(np) && fv >= R(0) && fv < R(np)) {
+        const int64_t iu = (int64_t)floor(fu), iv = (int64_t)floor(fv);
+        atomicAdd(P.t.cam_image + P.cam[cam].img_off + (iv * np + iu) * P.cam_nb + bin, w);
+      }
     }
-    st_spec = nullptr;
-    st_img = nullptr;
   };
 
   auto finish = [&](int status, double sfreq) {
@@ -122,7 +136,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     if (P.t.pk_status) {
       P.t.pk_status[pid] = status;
       P.t.pk_nscat[pid] = nscat;
-      P.t.pk_freq[pid] = status == 1 ? sfreq : 0.0;
+      P.t.pk_freq[pid] = sfreq;   // escape frequency; at the cap for max_scatter caps; else 0
     }
     alive = false;
   };
@@ -137,7 +151,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     for (int a = 0; a < 3; ++a) {
       e.ijk[a] = ci[a];
       e.xi[a] = xi[a];
-      e.pos[a] = G.lo[a] + ((double)ci[a] + (double)xi[a]) * G.h[a];
+      e.rel[a] = (R(ci[a]) + xi[a] - R(0.5) * R(G.n[a])) * R(G.h[a]);
       e.k[a] = kin ? kin[a] : R(0);
       e.ua[a] = ua ? ua[a] : R(0);
     }
@@ -148,6 +162,9 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     e.RQ = RQ;
     e.inv_vth = r0.w;
     e.u[0] = r1.x; e.u[1] = r1.y; e.u[2] = r1.z;
+    e.kHI = r0.x;
+    e.a = r0.y;
+    e.kd = r0.z;
   };
 
   for (;;) {
@@ -184,7 +201,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           m_sincospi(R(2) * b0.v[1], &sp, &cp);
           const R st = m_sqrt(fmax(R(0), R(1) - mu * mu));
           k[0] = st * cp; k[1] = st * sp; k[2] = mu;
-          tau = -log((double)b0.v[2]);
+          tau = (double)(-m_log(b0.v[2]));
           double r[3] = {P.src[0], P.src[1], P.src[2]};
           if (P.src_sigma > 0.0) {
             U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
@@ -311,7 +328,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         bool cont = true;
         if (b0.v[0] * ktot < R(r0.z)) {
           // dust: absorb with probability 1 - A, else isotropic scattering
-          if ((double)b0.v[1] >= P.albedo) {
+          if (b0.v[1] >= R(P.albedo)) {
             finish(2, 0.0);
             cont = false;
           } else {
@@ -355,96 +372,123 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         }
         if (cont) {
           if (P.max_scatter && nscat >= P.max_scatter) {
-            finish(3, 0.0);
+            // capped by the scattering limit: report the lab frequency at the cap
+            const double ku = (double)k[0] * r1.x + (double)k[1] * r1.y + (double)k[2] * r1.z;
+            finish(3, ((double)x + ku) / (double)r0.w * P.spec_scale);
           } else {
-            tau = -log((double)b0.v[2]);
+            tau = (double)(-m_log(b0.v[2]));
           }
         }
       }
     }
 
     // ------------------------------------------------------------ peel-off --
-    unsigned pm = __ballot_sync(kFull, has_peel);
+    // Phase 1 (per lane): the first cell of every camera ray is the event's own
+    //   cell, whose record the lane holds, so its optical depth costs no memory
+    //   access; a core photon's rays almost always pass tau_esc_max right there.
+    // Phase 2 (per lane): up to kLanePeel further cells, one lane per ray.
+    // Phase 3 (warp): rays still alive are marched by the whole warp, 32 cells
+    //   per step (coalesced records, butterfly sum, exit once tau > cutoff).
     __syncwarp();
-    while (pm) {
-      const int src = __ffs(pm) - 1;
-      pm &= pm - 1;
-      const PeelEv<R>& e = sev[src];
-      const Job* JE = L.jobs + e.job;
+    {
+      const PeelEv<R>& e = sev[lane];
+      const Job* JE = L.jobs + (has_peel ? e.job : 0);
       const GridDev& G = JE->g;
       const RunDev& P = JE->p;
-      const float4* __restrict__ rec = G.rec;
-      for (int cam = 0; cam < P.n_cam; ++cam) {
-        const int ax = P.cam[cam].axis;
-        const int s = P.cam[cam].sgn;
-        if (G.periodic_xy && ax < 2) continue;   // no observer along a periodic axis
-        R W = R(1), xc = e.x;
-        if (e.type == 1) {
-          const R mu_c = s > 0 ? e.k[ax] : -e.k[ax];
-          W = (R(1) + e.RQ * mu_c * mu_c) / (R(1) + e.RQ / R(3));
-          const R kcu = s > 0 ? e.ua[ax] : -e.ua[ax];
-          xc = e.x + kcu - e.upar + e.g * (mu_c - R(1));
-        }
-        const R us = s > 0 ? e.u[ax] : -e.u[ax];
-        // lab-frame Doppler velocity (km/s), invariant along the ray
-        const double V = ((double)xc + (double)us) / (double)e.inv_vth;
-        const int b = bin_of(V * P.cam_scale, P.cam_lo, P.cam_hi, P.cam_nb);
-        if (b < 0) continue;
-        const R Vr = (R)V;
-        const int start = e.ijk[ax];
-        const int remaining = s > 0 ? G.n[ax] - start : start + 1;
-        const int64_t step = (int64_t)s * G.stride[ax];
-        const R hax = R(G.h[ax]);
-        const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
+      const int ncam = has_peel ? P.n_cam : 0;
+      const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncam);
+      for (int cam = 0; cam < ncam_max; ++cam) {
+        bool act = cam < ncam;
+        int ax = 0, s = 1, bin = -1, remaining = 0;
+        R W = R(1), Vr = R(0);
         double tau_acc = 0.0;
-        bool cut = false;
-        for (int base = 0; base < remaining; base += 32) {
-          const int m = base + lane;
-          R tc = R(0);
-          if (m < remaining) {
-            const int64_t c = e.cell + step * m;
-            const float4 q0 = __ldg(rec + 2 * c);
-            const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * c + 1) + ax);
-            const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
-            const R Hc = voigt<R>(R(q0.y), xcell);
-            tc = (R(q0.x) * Hc + R(q0.z)) * (m == 0 ? l0 : hax);
-            lc[kPeelVisits]++;
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(kFull, tc, o);
-          tc = __shfl_sync(kFull, tc, 0);
-          tau_acc += (double)tc;
-          if (tau_acc > P.tau_max) { cut = true; break; }
+        int64_t cellp = 0, step = 0;
+        if (act) {
+          ax = P.cam[cam].axis;
+          s = P.cam[cam].sgn;
+          if (G.periodic_xy && ax < 2) act = false;   // no observer along a periodic axis
         }
-        if (lane == 0) lc[kPeelRays]++;
-        if (cut) continue;
-        const double w = (double)W * exp(-tau_acc);
-        // stage the tally on lane nq % 32
-        if (lane == (nq & 31)) {
-          const int64_t si = (int64_t)cam * P.cam_nb + b;
-          st_spec = P.t.cam_spec + si;
-          st_spec2 = P.t.cam_spec2 + si;
-          st_img = nullptr;
-          const int np = P.cam[cam].npix;
-          if (np > 0 && P.t.cam_image) {
-            const int au = (ax + 1) % 3, av = (ax + 2) % 3;
-            const double pu = s * (e.pos[au] - P.centre[au]);
-            const double pv = e.pos[av] - P.centre[av];
-            const double fu = (pu + P.fov_half) / (2.0 * P.fov_half) * np;
-            const double fv = (pv + P.fov_half) / (2.0 * P.fov_half) * np;
-            if (fu >= 0.0 && fu < np && fv >= 0.0 && fv < np) {
-              const int64_t iu = (int64_t)floor(fu), iv = (int64_t)floor(fv);
-              st_img = P.t.cam_image + P.cam[cam].img_off + (iv * np + iu) * P.cam_nb + b;
+        if (act) {
+          R xc = e.x;
+          if (e.type == 1) {
+            const R mu_c = s > 0 ? e.k[ax] : -e.k[ax];
+            W = (R(1) + e.RQ * mu_c * mu_c) / (R(1) + e.RQ / R(3));
+            const R kcu = s > 0 ? e.ua[ax] : -e.ua[ax];
+            xc = e.x + kcu - e.upar + e.g * (mu_c - R(1));
+          }
+          const R us = s > 0 ? e.u[ax] : -e.u[ax];
+          // lab-frame Doppler velocity (km/s), invariant along the ray
+          Vr = (xc + us) / e.inv_vth;
+          bin = bin_of_r<R>(Vr * R(P.cam_scale), R(P.cam_lo), R(P.cam_hi), R(P.cam_inv_width), P.cam_nb);
+          if (bin < 0) {
+            act = false;
+          } else {
+            const R hax = R(G.h[ax]);
+            const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
+            lc[kPeelRays]++;
+            lc[kPeelVisits]++;
+            tau_acc = (double)((e.kHI * voigt<R>(e.a, xc) + e.kd) * l0);
+            const int start = e.ijk[ax];
+            remaining = (s > 0 ? G.n[ax] - start : start + 1) - 1;
+            step = (int64_t)s * G.stride[ax];
+            cellp = e.cell + step;
+            if (tau_acc <= P.tau_max) {
+              const float4* __restrict__ rec = G.rec;
+              for (int j = 0; j < kLanePeel && remaining > 0; ++j) {
+                const float4 q0 = __ldg(rec + 2 * cellp);
+                const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * cellp + 1) + ax);
+                const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
+                tau_acc += (double)((R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * hax);
+                lc[kPeelVisits]++;
+                cellp += step;
+                --remaining;
+                if (tau_acc > P.tau_max) break;
+              }
+            }
+            if (tau_acc > P.tau_max) {
+              act = false;
+            } else if (remaining == 0) {
+              peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tau_acc))));
+              act = false;
             }
           }
-          st_w = w;
         }
-        ++nq;
-        if ((nq & 31) == 0) flush(32);
+        unsigned coop = __ballot_sync(kFull, act);
+        while (coop) {
+          const int src = __ffs(coop) - 1;
+          coop &= coop - 1;
+          const int64_t c0 = __shfl_sync(kFull, cellp, src);
+          const int64_t st = __shfl_sync(kFull, step, src);
+          const int rem = __shfl_sync(kFull, remaining, src);
+          const int axs = __shfl_sync(kFull, ax, src);
+          const int ss = __shfl_sync(kFull, s, src);
+          const R vv = __shfl_sync(kFull, Vr, src);
+          double tacc = __shfl_sync(kFull, tau_acc, src);
+          const Job* JS = L.jobs + __shfl_sync(kFull, has_peel ? e.job : 0, src);
+          const float4* __restrict__ rec = JS->g.rec;
+          const R hs = R(JS->g.h[axs]);
+          const double tmax = JS->p.tau_max;
+          bool cut = false;
+          for (int base = 0; base < rem; base += 32) {
+            const int m = base + lane;
+            R tc = R(0);
+            if (m < rem) {
+              const int64_t c = c0 + st * m;
+              const float4 q0 = __ldg(rec + 2 * c);
+              const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * c + 1) + axs);
+              const R xcell = vv * R(q0.w) - (ss > 0 ? R(uq) : R(-uq));
+              tc = (R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * hs;
+              lc[kPeelVisits]++;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(kFull, tc, o);
+            tacc += (double)__shfl_sync(kFull, tc, 0);
+            if (tacc > tmax) { cut = true; break; }
+          }
+          if (lane == src && !cut) peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tacc))));
+        }
       }
     }
-    if (nq & 31) flush(nq & 31);
-    nq = 0;
     __syncwarp();
   }
 
