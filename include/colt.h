@@ -216,6 +216,51 @@ int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, siz
 int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out);
 int colt_release(colt_ctx* ctx, colt_req req);
 
+/* --------------------------------------------- solve without allocating -- */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that runs under a device-memory
+ * budget owned by another allocator, or a library that must not call
+ * cudaMalloc on its user's behalf.  It performs the blocking batched solve of
+ * colt_run_batch with caller-owned inputs and outputs and calls no
+ * cudaMalloc, cudaFree or allocating routine, and needs no context.
+ *
+ * Inputs: n solves (1 <= n <= 8; larger n returns COLT_EINVAL), each a
+ * Cartesian grid given by its geometry and its DEVICE array of packed cell
+ * records (8 floats per cell, the layout colt_read_cells returns, including
+ * a tau_NL), and its run parameters (host).  Outputs: per solve, DEVICE
+ * tallies the caller allocated: spec [spec_nbins] and counters [8] (emitted,
+ * escaped, absorbed, capped, scatterings, HI scatterings, underflow,
+ * overflow) as unsigned 64-bit, cam_spec / cam_spec2 [n_cam * cam_nbins]
+ * (when n_cam > 0) and cam_image (when a camera has npix > 0) as doubles.
+ * The call zeroes these outputs, runs, and synchronises cuda_stream (NULL is
+ * the legacy default stream) before returning.  Returns COLT_EINVAL for bad
+ * sizes or parameters, COLT_ECUDA for a failed CUDA call, COLT_EDEVICE when
+ * the kernel's bounds checks fired.
+ *
+ * The launch header, job table and counters live in one static device array
+ * of 16 KB that every GPU loading the library keeps until process exit.  The
+ * first call on a device looks up that array's device address with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array, which keeps the last call's contents: calls that overlap
+ * on the GPU (from several threads or streams) race, so serialise them. */
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  int periodic_xy;
+  const float* records;     /* device, 8 floats per cell */
+} colt_grid_view;
+
+typedef struct {
+  unsigned long long* spec;
+  unsigned long long* counters;
+  double* cam_spec;
+  double* cam_spec2;
+  double* cam_image;
+} colt_device_tallies;
+
+int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_run_params* params,
+                     const colt_device_tallies* tallies, void* cuda_stream);
+
 /* ------------------------------------------------------ parity helpers -- */
 /* App. A1, Eq. AB: H_approx(a, x) for n pairs.  mem says where a, x, H live.
  * precision COLT_MIXED evaluates in FP32 on float arrays; COLT_PLAIN in FP64

@@ -27,7 +27,8 @@ COLT_PLAIN, COLT_MIXED = 0, 1
 
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
-           "colt_wait", "colt_read_spectrum", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter"]
+           "colt_wait", "colt_read_spectrum", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
+           "colt_run_noalloc"]
 
 _LIB = None
 
@@ -123,6 +124,7 @@ def lib():
             "colt_release": (I, [P, U64]),
             "colt_voigt": (I, [P, P, P, P, SZ, I, I]),
             "colt_scatter": (I, [P, P, SZ, U64, I]),
+            "colt_run_noalloc": (I, [I, P, P, P, P]),
         }
         for name, (rt, args) in sig.items():
             f = getattr(L, name)
@@ -361,6 +363,42 @@ def colt_read_result(ctx, req: int, spec) -> dict:
 
 def colt_release(ctx, req: int):
     _check(ctx, lib().colt_release(ctx, C.c_uint64(req)))
+
+
+# ---------------------------------------------------- solve without allocating --
+class GridView(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("periodic_xy", C.c_int), ("records", C.c_void_p)]
+
+
+class DeviceTallies(C.Structure):
+    _fields_ = [("spec", C.c_void_p), ("counters", C.c_void_p), ("cam_spec", C.c_void_p),
+                ("cam_spec2", C.c_void_p), ("cam_image", C.c_void_p)]
+
+
+def colt_run_noalloc(grids, records, specs, tallies, cuda_stream=None, images=False):
+    """Blocking solve(s) without device allocation.  grids: synth.Grid list
+    (geometry only); records: device tensors (8 floats per cell); tallies:
+    dicts of device tensors spec, counters, cam_spec, cam_spec2, cam_image.
+    Returns the C status code (0 = COLT_OK)."""
+    n = len(grids)
+    gv = (GridView * n)()
+    ps = (RunParams * n)()
+    ts = (DeviceTallies * n)()
+    keep = []
+    for i, (g, rec, sp, t) in enumerate(zip(grids, records, specs, tallies)):
+        gv[i].nx, gv[i].ny, gv[i].nz = [int(v) for v in g.shape]
+        gv[i].lo = (C.c_double * 3)(*[float(v) for v in g.lo])
+        gv[i].hi = (C.c_double * 3)(*[float(v) for v in g.hi])
+        gv[i].periodic_xy = int(bool(g.periodic_xy))
+        gv[i].records = rec.data_ptr()
+        p, cams = run_params(sp, images)
+        keep.append(cams)
+        ps[i] = p
+        for f in ("spec", "counters", "cam_spec", "cam_spec2", "cam_image"):
+            v = t.get(f)
+            setattr(ts[i], f, v.data_ptr() if v is not None else None)
+    return lib().colt_run_noalloc(n, gv, ps, ts, C.c_void_p(cuda_stream) if cuda_stream else None)
 
 
 # ------------------------------------------------------------------- parity --
