@@ -179,7 +179,10 @@ def run_single_case(args):
     ctx = C.colt_init(0)
     t, v = cases()[args.single_case]
     h = C.colt_create_grid(ctx, case_grid(t, v))
-    r = C.colt_run(ctx, h, case_spec(args.single_case, args.packets_per_case, 0, images=not args.no_images))
+    sp = case_spec(args.single_case, args.packets_per_case, 0, images=not args.no_images)
+    if args.max_scatter > 0:
+        sp.max_scatter = args.max_scatter      # bounded histories: steady-state profiles
+    r = C.colt_run(ctx, h, sp)
     print(json.dumps({"case": args.single_case, "packets": args.packets_per_case, "kernel_ms": r["kernel_ms"],
                       "scatterings": r["n_scat"], "peel_visits": r["n_peel_visits"],
                       "cell_visits": r["n_cell_visits"]}))
@@ -371,6 +374,7 @@ def main():
     ap.add_argument("--packets-per-case", type=int, default=125000)
     ap.add_argument("--ref-packets", type=int, default=64)
     ap.add_argument("--single-case", type=int, default=-1)
+    ap.add_argument("--max-scatter", type=int, default=0)
     ap.add_argument("--no-images", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

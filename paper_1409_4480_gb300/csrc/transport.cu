@@ -391,14 +391,27 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     //   per step (coalesced records, butterfly sum, exit once tau > cutoff).
     __syncwarp();
     {
-      const PeelEv<R>& e = sev[lane];
-      const Job* JE = L.jobs + (has_peel ? e.job : 0);
-      const GridDev& G = JE->g;
-      const RunDev& P = JE->p;
-      const int ncam = has_peel ? P.n_cam : 0;
-      const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncam);
-      for (int cam = 0; cam < ncam_max; ++cam) {
-        bool act = cam < ncam;
+      // (event, camera) pairs are spread over the lanes: a full warp gives each
+      // lane the rays of one event, a warp with few events (the tail of long
+      // histories) marches their rays on many lanes at once
+      const unsigned pm = __ballot_sync(kFull, has_peel);
+      const int ncl = has_peel ? L.jobs[sev[lane].job].p.n_cam : 0;
+      const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncl);
+      const int n_pairs = __popc(pm) * ncam_max;
+      for (int pbase = 0; pbase < n_pairs; pbase += 32) {
+        const int q = pbase + lane;
+        bool act = q < n_pairs;
+        int src = __ffs(pm) - 1, cam = 0;
+        if (act) {
+          const int k = q / ncam_max;
+          cam = q - k * ncam_max;
+          src = (int)__fns(pm, 0, k + 1);
+        }
+        const PeelEv<R>& e = sev[src];
+        const Job* JE = L.jobs + e.job;
+        const GridDev& G = JE->g;
+        const RunDev& P = JE->p;
+        if (act && cam >= P.n_cam) act = false;
         int ax = 0, s = 1, bin = -1, remaining = 0;
         R W = R(1), Vr = R(0);
         double tau_acc = 0.0;
@@ -455,16 +468,16 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         }
         unsigned coop = __ballot_sync(kFull, act);
         while (coop) {
-          const int src = __ffs(coop) - 1;
+          const int own = __ffs(coop) - 1;
           coop &= coop - 1;
-          const int64_t c0 = __shfl_sync(kFull, cellp, src);
-          const int64_t st = __shfl_sync(kFull, step, src);
-          const int rem = __shfl_sync(kFull, remaining, src);
-          const int axs = __shfl_sync(kFull, ax, src);
-          const int ss = __shfl_sync(kFull, s, src);
-          const R vv = __shfl_sync(kFull, Vr, src);
-          double tacc = __shfl_sync(kFull, tau_acc, src);
-          const Job* JS = L.jobs + __shfl_sync(kFull, has_peel ? e.job : 0, src);
+          const int64_t c0 = __shfl_sync(kFull, cellp, own);
+          const int64_t st = __shfl_sync(kFull, step, own);
+          const int rem = __shfl_sync(kFull, remaining, own);
+          const int axs = __shfl_sync(kFull, ax, own);
+          const int ss = __shfl_sync(kFull, s, own);
+          const R vv = __shfl_sync(kFull, Vr, own);
+          double tacc = __shfl_sync(kFull, tau_acc, own);
+          const Job* JS = L.jobs + __shfl_sync(kFull, e.job, own);
           const float4* __restrict__ rec = JS->g.rec;
           const R hs = R(JS->g.h[axs]);
           const double tmax = JS->p.tau_max;
@@ -485,7 +498,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             tacc += (double)__shfl_sync(kFull, tc, 0);
             if (tacc > tmax) { cut = true; break; }
           }
-          if (lane == src && !cut) peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tacc))));
+          if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tacc))));
         }
       }
     }

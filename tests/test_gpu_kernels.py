@@ -120,8 +120,11 @@ def test_scatter_step_parity(O, colt, ctx, precision, tol, max_bad):
     for i in np.flatnonzero(value_bad)[:6]:
         diffs = {f: float(np.max(np.abs(np.asarray(got[f][i]) - np.asarray(ref[f][i]))))
                  for f in ("x_f", "u_par", "u_atom", "k_f", "mu", "x_crit")}
-        detail.append(dict(x=float(inp["x"][i]), a=float(inp["a"][i]), atau0=float(inp["atau0"][i]),
-                           mu=float(ref["mu"][i]), **diffs))
+        worst = max(diffs, key=diffs.get)
+        detail.append(f"row {i}: worst {worst} diff {diffs[worst]:.3g} (x_f {diffs['x_f']:.2g}, "
+                      f"u_par {diffs['u_par']:.2g}, u_atom {diffs['u_atom']:.2g}, k_f {diffs['k_f']:.2g}); "
+                      f"x={inp['x'][i]:.7g} a={inp['a'][i]:.4g} atau0={inp['atau0'][i]:.4g} "
+                      f"u_par={ref['u_par'][i]:.7g} mu={ref['mu'][i]:.7g} trials={ref['n_trials'][i]}")
     if precision == 1:
         assert np.all(np.abs(ref["mu"][value_bad]) > 1 - 1e-3), detail
         assert np.count_nonzero(value_bad) <= 5e-5 * len(ok), detail
