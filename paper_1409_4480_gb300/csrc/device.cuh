@@ -89,7 +89,7 @@ struct VoigtCoef {
 };
 
 template <typename R>
-__device__ __forceinline__ R voigt(R a, R x) {
+__device__ __noinline__ R voigt(R a, R x) {
   using C = VoigtCoef;
   const R zh = x * x;
   const R zl = m_fma(x, x, -zh);
@@ -181,10 +181,14 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
       U4<R> q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
       ++t;
       const bool upper = p < q.v[0];
+      // psi = alpha R on the lower piece, alpha + (pi - alpha) R on the upper;
+      // past pi/2 the upper piece uses the exact complement
+      // pi - psi = (pi - alpha)(1 - R), so that sin stays well conditioned
       const R psi = upper ? m_fma(R(kPi) - alpha, q.v[1], alpha) : alpha * q.v[1];
+      const bool flip = upper && psi > R(0.5 * kPi);
       R s, c;
-      m_sincos(psi, &s, &c);
-      const R tt = a * c / s;          // |x| - u
+      m_sincos(flip ? (R(kPi) - alpha) * (R(1) - q.v[1]) : psi, &s, &c);
+      const R tt = flip ? -a * c / s : a * c / s;   // |x| - u
       u = xa - tt;
       // upper piece: exp(u0^2 - u^2) with u0 - u = tt - d, u0 + u = 2|x| - d - tt
       const R acc = upper ? m_exp((tt - d) * (R(2) * xa - d - tt)) : m_exp(-u * u);

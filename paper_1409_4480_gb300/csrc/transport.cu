@@ -414,7 +414,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         if (act && cam >= P.n_cam) act = false;
         int ax = 0, s = 1, bin = -1, remaining = 0;
         R W = R(1), Vr = R(0);
-        double tau_acc = 0.0;
+        R tau_acc = R(0);   // per-ray tau in the transport precision until the warp march
         int64_t cellp = 0, step = 0;
         if (act) {
           ax = P.cam[cam].axis;
@@ -440,25 +440,25 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
             lc[kPeelRays]++;
             lc[kPeelVisits]++;
-            tau_acc = (double)((e.kHI * voigt<R>(e.a, xc) + e.kd) * l0);
+            tau_acc = (e.kHI * voigt<R>(e.a, xc) + e.kd) * l0;
             const int start = e.ijk[ax];
             remaining = (s > 0 ? G.n[ax] - start : start + 1) - 1;
             step = (int64_t)s * G.stride[ax];
             cellp = e.cell + step;
-            if (tau_acc <= P.tau_max) {
+            if (tau_acc <= R(P.tau_max)) {
               const float4* __restrict__ rec = G.rec;
               for (int j = 0; j < kLanePeel && remaining > 0; ++j) {
                 const float4 q0 = __ldg(rec + 2 * cellp);
                 const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * cellp + 1) + ax);
                 const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
-                tau_acc += (double)((R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * hax);
+                tau_acc += (R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * hax;
                 lc[kPeelVisits]++;
                 cellp += step;
                 --remaining;
-                if (tau_acc > P.tau_max) break;
+                if (tau_acc > R(P.tau_max)) break;
               }
             }
-            if (tau_acc > P.tau_max) {
+            if (tau_acc > R(P.tau_max)) {
               act = false;
             } else if (remaining == 0) {
               peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tau_acc))));
@@ -476,7 +476,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           const int axs = __shfl_sync(kFull, ax, own);
           const int ss = __shfl_sync(kFull, s, own);
           const R vv = __shfl_sync(kFull, Vr, own);
-          double tacc = __shfl_sync(kFull, tau_acc, own);
+          double tacc = (double)__shfl_sync(kFull, tau_acc, own);
           const Job* JS = L.jobs + __shfl_sync(kFull, e.job, own);
           const float4* __restrict__ rec = JS->g.rec;
           const R hs = R(JS->g.h[axs]);
