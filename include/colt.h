@@ -205,10 +205,15 @@ typedef struct {
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);
-/* Drives the scheduler one step if work is pending and reports the request's
- * state; never blocks longer than one batched launch. */
+/* Drives the scheduler one step (collects finished launches, admits queued
+ * requests, refills free launch slots) and reports the request's state;
+ * never blocks on the device.  The scheduler advances only inside colt_submit,
+ * colt_poll and colt_wait. */
 int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st);
-/* Block until req is done or timeout_ms elapses (COLT_ETIMEOUT). */
+/* Block until req is done or timeout_ms (< 0: no limit) elapses
+ * (COLT_ETIMEOUT).  While waiting it sleeps until any in-flight launch
+ * finishes and then refills the free slot, so other requests keep the GPU
+ * busy; it re-polls at least every 20 ms. */
 int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms);
 /* camera = -1: the angle-averaged escape spectrum (as doubles); else the
  * camera's peel-off spectrum.  nbins must match the request's bin count. */

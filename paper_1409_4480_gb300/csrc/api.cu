@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -117,6 +118,11 @@ struct colt_ctx {
   Slot slots[kSlots];
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_alloc = nullptr;
   uint64_t launches = 0;                // transport kernel launches issued
+  // completion signal of serving launches: a host function enqueued behind
+  // each launch bumps done_seq, so colt_wait wakes when ANY slot finishes
+  std::mutex cv_mu;
+  std::condition_variable cv;
+  uint64_t done_seq = 0;
 };
 
 namespace {
@@ -508,6 +514,17 @@ int serve_admit(colt_ctx* ctx) {
   return admitted;
 }
 
+// Host function behind every serving launch (runs on a CUDA driver thread,
+// makes no CUDA calls).
+void CUDART_CB slot_done_cb(void* arg) {
+  colt_ctx* ctx = static_cast<colt_ctx*>(arg);
+  {
+    std::lock_guard<std::mutex> g(ctx->cv_mu);
+    ++ctx->done_seq;
+  }
+  ctx->cv.notify_all();
+}
+
 // Build and enqueue one batched launch on a free slot over admitted requests
 // with packets not yet handed out (oldest first), sharing a packet budget;
 // all jobs of a launch share one precision.  Returns 1 if launched.
@@ -557,6 +574,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   CU(cudaStreamWaitEvent(sl.stream, ctx->ev_alloc, 0));
   rc = enqueue_launch(ctx, si, prec, 0);
   if (rc) return rc;
+  CU(cudaLaunchHostFunc(sl.stream, slot_done_cb, ctx));
   CU(cudaEventRecord(sl.done, sl.stream));
   sl.in_flight = true;
   return 1;
@@ -849,22 +867,28 @@ int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms) {
   if (!ctx) return COLT_EINVAL;
   const double t0 = now_ms();
   for (;;) {
+    uint64_t seq;
+    {
+      std::lock_guard<std::mutex> g(ctx->cv_mu);
+      seq = ctx->done_seq;
+    }
     {
       std::lock_guard<std::recursive_mutex> lk(ctx->mu);
       int done = 0;
       int rc = colt_poll(ctx, req, &done, nullptr);
       if (rc) return rc;
       if (done) return COLT_OK;
-      // block on the oldest in-flight launch (bounded: one persistent launch)
-      int si = -1;
-      for (int k = 0; k < kSlots; ++k)
-        if (ctx->slots[k].in_flight) { si = k; break; }
-      if (si >= 0) {
-        cudaError_t e = cudaEventSynchronize(ctx->slots[si].done);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "serving launch");
-      }
     }
-    if (timeout_ms >= 0 && now_ms() - t0 > timeout_ms) return fail(ctx, COLT_ETIMEOUT, "colt_wait timed out");
+    double wait_ms = 20.0;   // re-poll at least this often (a queued request may wait on memory)
+    if (timeout_ms >= 0) {
+      const double left = timeout_ms - (now_ms() - t0);
+      if (left <= 0) return fail(ctx, COLT_ETIMEOUT, "colt_wait timed out");
+      wait_ms = std::min(wait_ms, left);
+    }
+    // sleep until any in-flight launch finishes (its host function bumps done_seq)
+    std::unique_lock<std::mutex> l(ctx->cv_mu);
+    ctx->cv.wait_for(l, std::chrono::duration<double, std::milli>(wait_ms),
+                     [&] { return ctx->done_seq != seq; });
   }
 }
 

@@ -34,6 +34,11 @@ __device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(
 __device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float m_copysign1(float v) { return copysignf(1.0f, v); }
 __device__ __forceinline__ double m_copysign1(double v) { return copysign(1.0, v); }
+// Division on the latency-critical path: in FP32 the hardware reciprocal
+// form (within 2 ulp for divisors of normal magnitude, which is all this code
+// divides by); in FP64 the correctly rounded quotient.
+__device__ __forceinline__ float m_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double m_div(double x, double y) { return x / y; }
 
 // ---------------------------------------------------------------- Philox --
 // Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11).
@@ -78,7 +83,8 @@ __device__ __forceinline__ U4<R> uniforms(const Rng& g, uint64_t pid, uint32_t e
 // App. A1, Eq. AB, Table AB.  The three continued fractions are evaluated as
 // single rational functions (one division each); z = x^2 is formed exactly as
 // z_hi + z_lo and the region is chosen from the exact z, and
-// exp(-z) = exp(-z_hi) (1 - z_lo).
+// exp(-z) = exp(-z_hi) (1 - z_lo).  Not inlined: the march and three peel-off
+// phases call it, and one copy keeps the kernel's instruction footprint small.
 struct VoigtCoef {
   static constexpr double A0 = 15.75328153963877, A1 = 286.9341762324778, A2 = 19.05706700907019,
                           A3 = 28.22644017233441, A4 = 9.526399802414186, A5 = 35.29217026286130,
@@ -100,7 +106,7 @@ __device__ __noinline__ R voigt(R a, R x) {
     const R d3 = z - R(C::A6);
     const R d2 = m_fma(z - R(C::A4), d3, R(C::A5));
     const R d1 = m_fma(z - R(C::A2), d2, R(C::A3) * d3);
-    const R cf = R(C::A1) * d2 / d1;
+    const R cf = m_div(R(C::A1) * d2, d1);
     const R ez = m_exp(-zh) * (R(1) - zl);
     return ez * (R(1) - a * (R(C::A0) + cf));
   } else if (mid) {
@@ -108,23 +114,23 @@ __device__ __noinline__ R voigt(R a, R x) {
     const R e3 = m_fma(z - R(C::B6), e4, R(C::B7));
     const R e2 = m_fma(z + R(C::B4), e3, R(C::B5) * e4);
     const R e1 = m_fma(z - R(C::B2), e2, R(C::B3) * e3);
-    const R cf = R(C::B1) * e2 / e1;
+    const R cf = m_div(R(C::B1) * e2, e1);
     const R ez = m_exp(-zh) * (R(1) - zl);
     return ez + a * (R(C::B0) + cf);
   } else if (z < R(1e10)) {
     const R f3 = z - R(5.5);
     const R f2 = m_fma(z - R(3.5), f3, R(-5));
     const R f1 = m_fma(z - R(1.5), f2, R(-1.5) * f3);
-    return (a * R(1.0 / kSqrtPi)) * f2 / f1;
+    return m_div((a * R(1.0 / kSqrtPi)) * f2, f1);
   } else {
-    return (a * R(1.0 / kSqrtPi)) / (z - R(1.5));
+    return m_div(a * R(1.0 / kSqrtPi), z - R(1.5));
   }
 }
 
 // Sec. 3.2.2, Eq. xcw: rational fit in the natural log of a.
 template <typename R>
 __device__ __forceinline__ R x_cw_fit(R a) {
-  return R(6.9184721) + R(81.766279) / (m_log(a) - R(14.651253));
+  return R(6.9184721) + m_div(R(81.766279), m_log(a) - R(14.651253));
 }
 
 // Sec. 3.2.4, Eq. xcrit.
@@ -135,9 +141,10 @@ __device__ __forceinline__ R x_crit_of(R atau0) {
 
 // ---------------------------------------------------------------- u_par --
 // Sec. 3.2.3.  Draws for |x|, sign restored at the end.  Trial t uses Philox
-// block 2 + t of the event.  The proposal angle is carried as
-// psi = theta + pi/2 in (0, pi), so that tan(theta) = -cos(psi)/sin(psi) is
-// well conditioned near theta = +-pi/2 in FP32:
+// block 2 + t of the event; the caller passes block 2 (computed alongside the
+// event's other blocks).  The proposal angle is carried as psi = theta + pi/2
+// in (0, pi), so that tan(theta) = -cos(psi)/sin(psi) is well conditioned near
+// theta = +-pi/2 in FP32:
 //   |x| <= 1        : psi = pi R
 //   lower piece     : psi = alpha R,                 alpha = theta0 + pi/2
 //   upper piece     : psi = alpha + (pi - alpha) R
@@ -145,40 +152,41 @@ __device__ __forceinline__ R x_crit_of(R atau0) {
 // algebraically the paper's theta0 and p.
 template <typename R>
 __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64_t pid, uint32_t event,
-                                         int* n_trials) {
+                                         const U4<R>& first, int* n_trials) {
   const R xa = fabs(x);
   R u = R(0);
   if (xa >= R(9)) {
-    U4<R> q = uniforms<R>(rng, pid, event, 2);
     R s, c;
-    m_sincospi(R(2) * q.v[1], &s, &c);
-    u = R(1) / xa + m_sqrt(-m_log(q.v[0])) * c;
+    m_sincospi(R(2) * first.v[1], &s, &c);
+    u = m_div(R(1), xa) + m_sqrt(-m_log(first.v[0])) * c;
     *n_trials = 1;
   } else if (xa <= R(1)) {
     int t = 0;
+    U4<R> q = first;
     for (;;) {
       if (t >= kMaxTrials) { *n_trials = kMaxTrials + 1; break; }
-      U4<R> q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
+      if (t > 0) q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
       ++t;
       R s, c;
       m_sincospi(q.v[0], &s, &c);
-      u = xa - a * c / s;
+      u = xa - m_div(a * c, s);
       if (q.v[1] < m_exp(-u * u)) { *n_trials = t; break; }
     }
   } else {
     // d = |x| - u0 taken straight from the two u0 forms (u0_core = x - 1/(x +
     // e^{1-x^2}/a), u0_wing = x_cw - 1/x_cw + 0.15 (x - x_cw)): forming it as
     // |x| - u0 would cancel (d ~ a near |x| = 1) and cost FP32 its accuracy
-    const R d = (xa < xcw) ? R(1) / (xa + m_exp(R(1) - xa * xa) / a)
-                           : R(0.85) * (xa - xcw) + R(1) / xcw;
+    const R d = (xa < xcw) ? m_div(R(1), xa + m_div(m_exp(R(1) - xa * xa), a))
+                           : R(0.85) * (xa - xcw) + m_div(R(1), xcw);
     const R u0 = xa - d;
     const R alpha = m_atan2(a, d);
     const R e0 = m_exp(-u0 * u0);
-    const R p = alpha / ((R(1) - e0) * alpha + e0 * R(kPi));
+    const R p = m_div(alpha, (R(1) - e0) * alpha + e0 * R(kPi));
     int t = 0;
+    U4<R> q = first;
     for (;;) {
       if (t >= kMaxTrials) { *n_trials = kMaxTrials + 1; break; }
-      U4<R> q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
+      if (t > 0) q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
       ++t;
       const bool upper = p < q.v[0];
       // psi = alpha R on the lower piece, alpha + (pi - alpha) R on the upper;
@@ -188,7 +196,7 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
       const bool flip = upper && psi > R(0.5 * kPi);
       R s, c;
       m_sincos(flip ? (R(kPi) - alpha) * (R(1) - q.v[1]) : psi, &s, &c);
-      const R tt = flip ? -a * c / s : a * c / s;   // |x| - u
+      const R tt = flip ? -m_div(a * c, s) : m_div(a * c, s);   // |x| - u
       u = xa - tt;
       // upper piece: exp(u0^2 - u^2) with u0 - u = tt - d, u0 + u = 2|x| - d - tt
       const R acc = upper ? m_exp((tt - d) * (R(2) * xa - d - tt)) : m_exp(-u * u);
@@ -203,11 +211,10 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
 template <typename R>
 __device__ __forceinline__ R sample_mu(R RQ, R u) {
   if (RQ == R(0)) return R(2) * u - R(1);
-  const R c = (R(2) * u - R(1)) * (R(1) + RQ / R(3));
-  const R p = R(3) / RQ;                    // mu^3 + p mu + q = 0, q = -p c
-  const R sp3 = m_sqrt(p / R(3));
+  const R c = (R(2) * u - R(1)) * (R(1) + RQ * R(1.0 / 3.0));
+  const R sp3 = m_sqrt(m_div(R(1), RQ));    // sqrt(p/3), p = 3/RQ; mu^3 + p mu - p c = 0
   // root = -2 sqrt(p/3) sinh( asinh( (3q/(2p)) sqrt(3/p) ) / 3 ),  3q/(2p) = -1.5 c
-  return R(2) * sp3 * m_sinh(m_asinh(R(1.5) * c / sp3) / R(3));
+  return R(2) * sp3 * m_sinh(m_asinh(m_div(R(1.5) * c, sp3)) * R(1.0 / 3.0));
 }
 
 // Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin (2017),
@@ -215,15 +222,16 @@ __device__ __forceinline__ R sample_mu(R RQ, R u) {
 template <typename R>
 __device__ __forceinline__ void onb(const R n[3], R e1[3], R e2[3]) {
   const R s = m_copysign1(n[2]);
-  const R aa = R(-1) / (s + n[2]);
+  const R aa = m_div(R(-1), s + n[2]);
   const R bb = n[0] * n[1] * aa;
   e1[0] = R(1) + s * n[0] * n[0] * aa; e1[1] = s * bb; e1[2] = -s * n[0];
   e2[0] = bb; e2[1] = s + n[1] * n[1] * aa; e2[2] = -n[1];
 }
 
-// One resonant scattering (Sec. 3.1.3 with Sec. 3.2.3-3.2.4).  Draws:
-// event block 0 word 3 = core R/Q choice, block 1 = (u_perp R1, R2, mu, phi),
-// blocks 2.. = u_par trials.  Returns outgoing direction, atom velocity and x_f.
+// One resonant scattering (Sec. 3.1.3 with Sec. 3.2.3-3.2.4).  The caller
+// passes the event's draw blocks 0 (word 3: core R/Q choice), 1 (u_perp R1,
+// R2, mu, phi) and 2 (first u_par trial); later trials draw blocks 3, 4, ...
+// Returns outgoing direction, atom velocity and x_f.
 template <typename R>
 struct ScatterOut {
   R x_f, k_f[3], u_atom[3], u_par, x_crit, RQ, mu;
@@ -233,20 +241,19 @@ struct ScatterOut {
 template <typename R>
 __device__ __forceinline__ ScatterOut<R> scatter_hi(R x, const R k[3], R a, R g, R atau0, int phase,
                                                     const Rng& rng, uint64_t pid, uint32_t event,
-                                                    R core_choice) {
+                                                    R core_choice, const U4<R>& b1, const U4<R>& b2) {
   ScatterOut<R> o;
   const R xcw = x_cw_fit<R>(a);
   R xc = atau0 >= R(0) ? x_crit_of<R>(atau0) : R(0);
   if (fabs(x) >= xc) xc = R(0);
   o.x_crit = xc;
-  U4<R> b1 = uniforms<R>(rng, pid, event, 1);
   // u_perp: truncated Box-Muller (Sec. 3.2.4)
   const R rho = m_sqrt(m_fma(xc, xc, -m_log(b1.v[0])));
   R s1, c1;
   m_sincospi(R(2) * b1.v[1], &s1, &c1);
   const R up1 = rho * c1, up2 = rho * s1;
   int nt = 0;
-  const R upar = sample_upar<R>(x, a, xcw, rng, pid, event, &nt);
+  const R upar = sample_upar<R>(x, a, xcw, rng, pid, event, b2, &nt);
   o.n_trials = nt;
   o.u_par = upar;
   R RQ;

@@ -34,8 +34,10 @@ __global__ void k_scatter(colt_scatter_io* io, size_t n, Rng rng) {
   const R k[3] = {R(v.k[0]), R(v.k[1]), R(v.k[2])};
   // the interaction's block 0 carries the core R/Q choice in its last word
   const U4<R> b0 = uniforms<R>(rng, v.pid, v.event, 0);
+  const U4<R> b1 = uniforms<R>(rng, v.pid, v.event, 1);
+  const U4<R> b2 = uniforms<R>(rng, v.pid, v.event, 2);
   const ScatterOut<R> o = scatter_hi<R>(R(v.x), k, R(v.a), R(v.g), R(v.atau0), v.phase, rng, v.pid, v.event,
-                                        b0.v[3]);
+                                        b0.v[3], b1, b2);
   v.x_f = o.x_f;
   for (int q = 0; q < 3; ++q) {
     v.k_f[q] = o.k_f[q];

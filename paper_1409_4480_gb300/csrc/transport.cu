@@ -23,6 +23,8 @@
 //     (coalesced 32-byte records), with a butterfly sum of the cell optical
 //     depths and an early exit once tau_esc exceeds the cutoff.
 //   * Tally atomics are staged one per lane and issued 32 at a time.
+#include <cstdio>
+
 #include "internal.h"
 
 namespace colt {
@@ -167,6 +169,24 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     e.kd = r0.z;
   };
 
+#ifdef COLT_PHASE_CLOCKS
+  // opt-in profiling build: SM cycles per phase of a round, summed over warps
+  // into launch counters 3.. (refill, flight + interaction, peel-off, rounds)
+  unsigned long long ph[4] = {0, 0, 0, 0};
+  long long t_mark = clock64();
+#define COLT_PHASE(i)                                  \
+  do {                                                 \
+    __syncwarp();                                      \
+    const long long t_now = clock64();                 \
+    ph[i] += (unsigned long long)(t_now - t_mark);     \
+    t_mark = t_now;                                    \
+  } while (0)
+#else
+#define COLT_PHASE(i) \
+  do {                \
+  } while (0)
+#endif
+
   for (;;) {
     bool has_peel = false;
     // ---------------------------------------------------------- refill --
@@ -245,6 +265,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       }
     }
     if (__all_sync(kFull, done)) break;
+    COLT_PHASE(0);
 
     // ------------------------------------------------ flight + interaction --
     // (a packet emitted this round makes its first flight next round)
@@ -253,11 +274,13 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       const RunDev& P = J->p;
       const float4* __restrict__ rec = G.rec;
       const uint64_t rpid = pid + P.pid_offset;
-      R hh[3], ik[3];
+      // per flight: cell size, inverse direction, direction in cell units
+      R hh[3], ik[3], kh[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         hh[a] = R(G.h[a]);
         ik[a] = k[a] != R(0) ? R(1) / k[a] : R(0);
+        kh[a] = k[a] / hh[a];
       }
       int64_t c = cell_index(G, ci);
       float4 r0 = __ldg(rec + 2 * c), r1 = __ldg(rec + 2 * c + 1);
@@ -284,13 +307,13 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         if (tau <= tau_cell) {
           const R le = R(tau) / ktot;
 #pragma unroll
-          for (int a = 0; a < 3; ++a) xi[a] += le * k[a] / hh[a];
+          for (int a = 0; a < 3; ++a) xi[a] += le * kh[a];
           interact = true;
           break;
         }
         tau -= tau_cell;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) if (a != ax) xi[a] += tmin * k[a] / hh[a];
+        for (int a = 0; a < 3; ++a) if (a != ax) xi[a] += tmin * kh[a];
         // cross the face on axis ax
         const int sgn = k[ax] > R(0) ? 1 : -1;
         int ni = ci[ax] + sgn;
@@ -323,7 +346,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         finish(1, V * P.spec_scale);
       } else if (interact) {
         ++event;
-        U4<R> b0 = uniforms<R>(P.rng, rpid, event, 0);
+        // the event's first three draw blocks are independent: compute them
+        // together (block 2 is the first u_par trial of a resonant scattering)
+        const U4<R> b0 = uniforms<R>(P.rng, rpid, event, 0);
+        const U4<R> b1 = uniforms<R>(P.rng, rpid, event, 1);
+        const U4<R> b2 = uniforms<R>(P.rng, rpid, event, 2);
         const R a = R(r0.y);
         bool cont = true;
         if (b0.v[0] * ktot < R(r0.z)) {
@@ -332,7 +359,6 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             finish(2, 0.0);
             cont = false;
           } else {
-            U4<R> b1 = uniforms<R>(P.rng, rpid, event, 1);
             if (P.n_cam > 0) {
               fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, r0, r1);
               has_peel = true;
@@ -354,7 +380,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             atau0 = a * R(r0.x) * lmin + R(r1.w);
           }
           const R g = P.recoil ? R(kGoverA) * a : R(0);
-          ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3]);
+          ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3], b1, b2);
           if (so.n_trials > kMaxTrials) {
             finish(3, 0.0);
             cont = false;
@@ -394,6 +420,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       // (event, camera) pairs are spread over the lanes: a full warp gives each
       // lane the rays of one event, a warp with few events (the tail of long
       // histories) marches their rays on many lanes at once
+      COLT_PHASE(1);
       const unsigned pm = __ballot_sync(kFull, has_peel);
       const int ncl = has_peel ? L.jobs[sev[lane].job].p.n_cam : 0;
       const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncl);
@@ -503,6 +530,10 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       }
     }
     __syncwarp();
+    COLT_PHASE(2);
+#ifdef COLT_PHASE_CLOCKS
+    ph[3] += 1;
+#endif
   }
 
 #pragma unroll
@@ -510,6 +541,15 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     const unsigned long long v = warp_sum_ull(lc[i]);
     if (lane == 0 && v) atomicAdd(L.counters + i, v);
   }
+#ifdef COLT_PHASE_CLOCKS
+  if (lane == 0) {
+    for (int i = 0; i < 4; ++i) atomicAdd(L.counters + kNumLaunchCounters + i, ph[i]);
+    if (ph[3] > 64)
+      printf("phase cycles per round: refill %.0f  flight+interaction %.0f  peel %.0f  (rounds %llu)\n",
+             (double)ph[0] / ph[3], (double)ph[1] / ph[3], (double)ph[2] / ph[3], ph[3]);
+  }
+#endif
+#undef COLT_PHASE
 }
 
 template <typename R>
