@@ -32,6 +32,8 @@ namespace {
 constexpr int kMaxJobs = 256;                  // solves per persistent launch
 constexpr int kSlots = 3;                      // launches in flight (serving)
 constexpr uint64_t kStepPackets = 1ull << 20;  // packet budget of one serving launch
+constexpr int kWorkWords = 8;                  // work counter + launch counters (+ phase clocks)
+constexpr int kMaxPassed = 4;                  // launches a ready request may be passed over
 
 double now_ms() {
   using namespace std::chrono;
@@ -42,14 +44,25 @@ struct GridObj {
   GridDev dev;
   float4* rec = nullptr;
   size_t bytes = 0;
+  // longest history (scatterings) any finished solve on this grid has had
+  uint64_t longest = 0;
+  bool measured = false;
 };
+
+// Longest-expected-first ordering of the jobs of a launch: the persistent
+// kernel hands out packets in job order, so a job whose histories can be very
+// long should start first, letting its longest packet overlap the rest of the
+// launch instead of running alone at the end (LPT scheduling).  A grid that
+// has never run sorts first.
+uint64_t grid_cost(const GridObj& g) { return g.measured ? g.longest : ~0ull; }
 
 // Device + pinned staging for one persistent launch: header, job_end, jobs.
 struct LaunchBuf {
   unsigned char* host = nullptr;        // pinned
   unsigned char* dev = nullptr;
   size_t bytes = 0;
-  unsigned long long* work = nullptr;   // device: next counter + launch counters
+  unsigned long long* work = nullptr;   // device: next counter + launch counters, then job_max
+  unsigned long long* jmax_h = nullptr; // pinned copy of job_max after the launch
   int* error = nullptr;
   LaunchDev* hdr_h() { return reinterpret_cast<LaunchDev*>(host); }
   unsigned long long* end_h() { return reinterpret_cast<unsigned long long*>(host + 256); }
@@ -92,6 +105,7 @@ struct Req {
   RunDev run;                           // tally pointers filled at admission
   Tally tally;
   int state = kQueued;
+  int passed = 0;                       // launches built while it was ready but left out
   uint64_t next_local = 0;              // packets handed to launches
   uint64_t done_packets = 0;
   double t_submit = 0, t_done = 0;
@@ -301,7 +315,8 @@ int ensure_slot(colt_ctx* ctx, int si) {
   lb.bytes = lb.off_jobs() + sizeof(Job) * kMaxJobs;
   CU(cudaMallocHost(&lb.host, lb.bytes));
   CU(cudaMalloc(&lb.dev, lb.bytes));
-  CU(cudaMalloc(&lb.work, sizeof(unsigned long long) * 8));
+  CU(cudaMalloc(&lb.work, sizeof(unsigned long long) * (kWorkWords + kMaxJobs)));
+  CU(cudaMallocHost(&lb.jmax_h, sizeof(unsigned long long) * kMaxJobs));
   CU(cudaMalloc(&lb.error, sizeof(int)));
   CU(cudaMemset(lb.error, 0, sizeof(int)));
   std::memset(lb.host, 0, lb.bytes);
@@ -311,6 +326,7 @@ int ensure_slot(colt_ctx* ctx, int si) {
   h->next = lb.work;
   h->counters = lb.work + 1;
   h->error = lb.error;
+  h->job_max = lb.work + kWorkWords;
   return COLT_OK;
 }
 
@@ -324,18 +340,22 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int blocks_per_sm) {
   ++ctx->launches;
   if (blocks_per_sm > 0) {
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
-    CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, sl.stream));
+    CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
     CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, blocks_per_sm, ctx->sm_count,
                         sl.stream));
+    CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
+                       cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
   }
   if (!sl.graph[gi]) {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
-    cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * 8, sl.stream);
+    cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
     cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, 0, ctx->sm_count,
                                       sl.stream);
+    cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
+                    cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "transport launch (capture)");
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
@@ -461,15 +481,25 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
 }
 
 // ----------------------------------------------------------- serving core --
+// Record the longest history a finished job saw on its grid.
+void learn_cost(colt_ctx* ctx, colt_grid grid, uint64_t longest) {
+  auto g = ctx->grids.find(grid);
+  if (g == ctx->grids.end()) return;
+  g->second.longest = std::max(g->second.longest, longest);
+  g->second.measured = true;
+}
+
 // A slot's launch finished: account its packets to its requests.
 int complete_slot(colt_ctx* ctx, int si) {
   Slot& sl = ctx->slots[si];
   sl.in_flight = false;
   const double t = now_ms();
-  for (auto& jp : sl.jobs) {
+  for (size_t j = 0; j < sl.jobs.size(); ++j) {
+    const auto& jp = sl.jobs[j];
     auto it = ctx->reqs.find(jp.first);
     if (it == ctx->reqs.end()) continue;
     Req& r = *it->second;
+    learn_cost(ctx, r.grid, sl.lb.jmax_h[j]);
     r.done_packets += jp.second;
     if (r.done_packets >= r.p.n_packets && r.state == kAdmitted) {
       r.state = kDone;
@@ -534,7 +564,21 @@ int serve_launch(colt_ctx* ctx, int si) {
     if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->p.n_packets)
       act.push_back(kv.second.get());
   if (act.empty()) return 0;
-  std::sort(act.begin(), act.end(), [](Req* a, Req* b) { return a->id < b->id; });
+  // requests passed over kMaxPassed times first (oldest first), then
+  // longest-expected-first, then oldest first
+  auto cost = [&](const Req* r) {
+    auto g = ctx->grids.find(r->grid);
+    return g == ctx->grids.end() ? 0ull : grid_cost(g->second);
+  };
+  std::sort(act.begin(), act.end(), [&](const Req* a, const Req* b) {
+    const bool aa = a->passed >= kMaxPassed, ab = b->passed >= kMaxPassed;
+    if (aa != ab) return aa;
+    if (!aa) {
+      const uint64_t ca = cost(a), cb = cost(b);
+      if (ca != cb) return ca > cb;
+    }
+    return a->id < b->id;
+  });
   const int prec = act.front()->p.precision;
   std::vector<Req*> sel;
   for (Req* r : act)
@@ -567,6 +611,11 @@ int serve_launch(colt_ctx* ctx, int si) {
     ++nj;
   }
   if (nj == 0) return 0;
+  for (Req* r : act)
+    if (std::none_of(sl.jobs.begin(), sl.jobs.end(), [&](const std::pair<uint64_t, uint64_t>& j) {
+          return j.first == r->id;
+        }))
+      ++r->passed;
   LaunchDev* h = lb.hdr_h();
   h->n_jobs = nj;
   h->total = total;
@@ -659,6 +708,7 @@ void colt_finalize(colt_ctx* ctx) {
       if (sl.lb.host) cudaFreeHost(sl.lb.host);
       if (sl.lb.dev) cudaFree(sl.lb.dev);
       if (sl.lb.work) cudaFree(sl.lb.work);
+      if (sl.lb.jmax_h) cudaFreeHost(sl.lb.jmax_h);
       if (sl.lb.error) cudaFree(sl.lb.error);
       if (sl.done) cudaEventDestroy(sl.done);
       if (sl.own_stream) cudaStreamDestroy(sl.stream);
@@ -755,16 +805,21 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   rc = ensure_slot(ctx, 0);
   if (rc) return rc;
   LaunchBuf& lb = ctx->slots[0].lb;
+  // job table in longest-expected-first order; results stay indexed by i
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return grid_cost(*gs[a]) > grid_cost(*gs[b]); });
   unsigned long long total = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int q = 0; q < n; ++q) {
+    const int i = ord[q];
     rc = alloc_tally(ctx, &params[i], per_packet[i], &ts[i]);
     if (rc) { free_all(); return rc; }
-    Job& J = lb.jobs_h()[i];
+    Job& J = lb.jobs_h()[q];
     J.g = gs[i]->dev;
     J.p = make_run(*gs[i], &params[i]);
     attach_tally(&J.p, ts[i]);
     total += params[i].n_packets;
-    lb.end_h()[i] = total;
+    lb.end_h()[q] = total;
   }
   LaunchDev* h = lb.hdr_h();
   h->n_jobs = n;
@@ -782,6 +837,8 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   }
   rc = check_device_error(ctx, 0);
+  if (total > 0 && !rc)
+    for (int q = 0; q < n; ++q) learn_cost(ctx, grids[ord[q]], lb.jmax_h[q]);
   for (int i = 0; i < n && !rc; ++i) {
     rc = copy_result(ctx, &params[i], ts[i], &out[i], per_packet[i]);
     out[i].kernel_ms = ms;

@@ -96,6 +96,7 @@ struct LaunchDev {
   unsigned long long* next = nullptr;        // work counter
   unsigned long long* counters = nullptr;    // [kNumLaunchCounters]
   int* error = nullptr;                      // device-side error flag
+  unsigned long long* job_max = nullptr;     // [n_jobs] longest history (scatterings), or null
 };
 
 // launchers (transport.cu)

@@ -67,6 +67,41 @@ __device__ __forceinline__ int bin_of_r(R s, R lo, R hi, R inv_width, int nb) {
   return (b >= 0 && b < nb) ? b : -1;
 }
 
+// Remaining optical depth of a flight (Sec. 3.1.2: tau_event = -ln R, less
+// the depth of every cell crossed).  The FP64 path keeps it in FP64.  The FP32
+// path keeps it as an unevaluated float pair hi + lo, updated with Knuth's
+// two-sum, so that many small cell depths subtract with ~48-bit accuracy on
+// the FP32 pipe (GB300's FP64 pipe issues 1/64 of the FP32 rate).
+template <typename R>
+struct TauLeft {
+  double v;
+  __device__ __forceinline__ void set(R t) { v = (double)t; }
+  __device__ __forceinline__ R value() const { return R(v); }
+  // true (state kept) when the remaining depth is at most c; else subtract c
+  __device__ __forceinline__ bool reached(R c) {
+    if (v <= (double)c) return true;
+    v -= (double)c;
+    return false;
+  }
+};
+
+template <>
+struct TauLeft<float> {
+  float hi, lo;
+  __device__ __forceinline__ void set(float t) { hi = t; lo = 0.f; }
+  __device__ __forceinline__ float value() const { return hi + lo; }
+  __device__ __forceinline__ bool reached(float c) {
+    const float s = __fsub_rn(hi, c);          // two-sum: s + e == hi - c exactly
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(-c, bb));
+    const float t = __fadd_rn(e, lo);
+    if (__fadd_rn(s, t) <= 0.f) return true;
+    hi = __fadd_rn(s, t);                      // renormalise (fast two-sum)
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+    return false;
+  }
+};
+
 __device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -97,14 +132,16 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   R xi[3] = {0, 0, 0};
   R k[3] = {0, 0, 1};
   R x = 0;
-  double tau = 0;
+  TauLeft<R> tau;
+  tau.set(R(0));
 
   // one peel-off contribution W exp(-tau_esc) into the camera spectrum (and
   // its square) and, inside the field of view, the image cube (Eq. SB)
-  auto peel_tally = [&](const RunDev& P, const PeelEv<R>& e, int cam, int ax, int s, int bin, double w) {
+  auto peel_tally = [&](const RunDev& P, const PeelEv<R>& e, int cam, int ax, int s, int bin, R wr) {
     const int64_t si = (int64_t)cam * P.cam_nb + bin;
+    const double w = (double)wr;
     atomicAdd(P.t.cam_spec + si, w);
-    atomicAdd(P.t.cam_spec2 + si, w * w);
+    atomicAdd(P.t.cam_spec2 + si, (double)(wr * wr));
     const int np = P.cam[cam].npix;
     if (np > 0 && P.t.cam_image) {
       const int au = (ax + 1) % 3, av = (ax + 2) % 3;
@@ -134,6 +171,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       atomicAdd(C + kCapped, 1ull);
     }
     if (nscat) atomicAdd(C + kScat, (unsigned long long)nscat);
+    if (L.job_max && nscat) atomicMax(L.job_max + jb, (unsigned long long)nscat);
     if (nscat_hi) atomicAdd(C + kScatHI, (unsigned long long)nscat_hi);
     if (P.t.pk_status) {
       P.t.pk_status[pid] = status;
@@ -170,9 +208,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   };
 
 #ifdef COLT_PHASE_CLOCKS
-  // opt-in profiling build: SM cycles per phase of a round, summed over warps
-  // into launch counters 3.. (refill, flight + interaction, peel-off, rounds)
-  unsigned long long ph[4] = {0, 0, 0, 0};
+  // opt-in profiling build: SM cycles per phase of a round, printed per warp
+  // (the lane maximum of each phase, exact for a warp with one live packet):
+  // 0 refill, 1 rest of the interaction, 2 peel-off, 3 rounds, 4 flight,
+  // 5 the event's draws, 6 the resonant scattering
+  unsigned long long ph[7] = {0, 0, 0, 0, 0, 0, 0};
   long long t_mark = clock64();
 #define COLT_PHASE(i)                                  \
   do {                                                 \
@@ -181,9 +221,18 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     ph[i] += (unsigned long long)(t_now - t_mark);     \
     t_mark = t_now;                                    \
   } while (0)
+#define COLT_MARK(i)                                   \
+  do {                                                 \
+    const long long t_now = clock64();                 \
+    ph[i] += (unsigned long long)(t_now - t_mark);     \
+    t_mark = t_now;                                    \
+  } while (0)
 #else
 #define COLT_PHASE(i) \
   do {                \
+  } while (0)
+#define COLT_MARK(i) \
+  do {               \
   } while (0)
 #endif
 
@@ -221,7 +270,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           m_sincospi(R(2) * b0.v[1], &sp, &cp);
           const R st = m_sqrt(fmax(R(0), R(1) - mu * mu));
           k[0] = st * cp; k[1] = st * sp; k[2] = mu;
-          tau = (double)(-m_log(b0.v[2]));
+          tau.set(-m_log(b0.v[2]));
           double r[3] = {P.src[0], P.src[1], P.src[2]};
           if (P.src_sigma > 0.0) {
             U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
@@ -303,15 +352,13 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             if (d < tmin) { tmin = d; ax = a; }
           }
         }
-        const double tau_cell = (double)(ktot * tmin);
-        if (tau <= tau_cell) {
-          const R le = R(tau) / ktot;
+        if (tau.reached(ktot * tmin)) {
+          const R le = tau.value() / ktot;
 #pragma unroll
           for (int a = 0; a < 3; ++a) xi[a] += le * kh[a];
           interact = true;
           break;
         }
-        tau -= tau_cell;
 #pragma unroll
         for (int a = 0; a < 3; ++a) if (a != ax) xi[a] += tmin * kh[a];
         // cross the face on axis ax
@@ -337,6 +384,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         x = (x + ku_old) * (R(r0.w) / ivth_old) - ku_new;
       }
       lc[kCellVisits] += visits;
+      COLT_MARK(4);
       if (status == 3) {
         finish(3, 0.0);
       } else if (escaped) {
@@ -351,6 +399,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         const U4<R> b0 = uniforms<R>(P.rng, rpid, event, 0);
         const U4<R> b1 = uniforms<R>(P.rng, rpid, event, 1);
         const U4<R> b2 = uniforms<R>(P.rng, rpid, event, 2);
+        COLT_MARK(5);
         const R a = R(r0.y);
         bool cont = true;
         if (b0.v[0] * ktot < R(r0.z)) {
@@ -381,6 +430,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           }
           const R g = P.recoil ? R(kGoverA) * a : R(0);
           ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3], b1, b2);
+          COLT_MARK(6);
           if (so.n_trials > kMaxTrials) {
             finish(3, 0.0);
             cont = false;
@@ -402,7 +452,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             const double ku = (double)k[0] * r1.x + (double)k[1] * r1.y + (double)k[2] * r1.z;
             finish(3, ((double)x + ku) / (double)r0.w * P.spec_scale);
           } else {
-            tau = (double)(-m_log(b0.v[2]));
+            tau.set(-m_log(b0.v[2]));
           }
         }
       }
@@ -488,7 +538,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             if (tau_acc > R(P.tau_max)) {
               act = false;
             } else if (remaining == 0) {
-              peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tau_acc))));
+              peel_tally(P, e, cam, ax, s, bin, W * m_exp(-R(tau_acc)));
               act = false;
             }
           }
@@ -525,7 +575,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             tacc += (double)__shfl_sync(kFull, tc, 0);
             if (tacc > tmax) { cut = true; break; }
           }
-          if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, (double)(W * m_exp(-R(tacc))));
+          if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, W * m_exp(-R(tacc)));
         }
       }
     }
@@ -542,14 +592,17 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     if (lane == 0 && v) atomicAdd(L.counters + i, v);
   }
 #ifdef COLT_PHASE_CLOCKS
-  if (lane == 0) {
-    for (int i = 0; i < 4; ++i) atomicAdd(L.counters + kNumLaunchCounters + i, ph[i]);
-    if (ph[3] > 64)
-      printf("phase cycles per round: refill %.0f  flight+interaction %.0f  peel %.0f  (rounds %llu)\n",
-             (double)ph[0] / ph[3], (double)ph[1] / ph[3], (double)ph[2] / ph[3], ph[3]);
+  for (int i = 0; i < 7; ++i)
+    for (int o = 16; o > 0; o >>= 1) ph[i] = max(ph[i], __shfl_xor_sync(kFull, ph[i], o));
+  if (lane == 0 && ph[3] > 64) {
+    const double r = (double)ph[3];
+    printf("phase cycles per round: refill %.0f  flight %.0f  draws %.0f  scatter %.0f  interaction-rest %.0f  "
+           "peel %.0f  (rounds %llu)\n",
+           ph[0] / r, ph[4] / r, ph[5] / r, ph[6] / r, ph[1] / r, ph[2] / r, ph[3]);
   }
 #endif
 #undef COLT_PHASE
+#undef COLT_MARK
 }
 
 template <typename R>
