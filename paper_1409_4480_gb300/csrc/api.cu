@@ -287,6 +287,7 @@ RunDev make_run(const GridObj& g, const colt_run_params* p) {
   r.fov_half = p->fov_half > 0 ? p->fov_half : fov;
   r.pix_scale = 0.5 / r.fov_half;
   r.cam_inv_width = p->cam_hi > p->cam_lo ? (double)r.cam_nb / (p->cam_hi - p->cam_lo) : 1.0;
+  fill_f32(r);
   return r;
 }
 
@@ -461,6 +462,7 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
     G.lo[a] = d->lo[a];
     G.hi[a] = d->hi[a];
     G.h[a] = (d->hi[a] - d->lo[a]) / G.n[a];
+    G.hf[a] = (float)G.h[a];
   }
   G.periodic_xy = d->periodic_xy ? 1 : 0;
   G.n_cells = n;

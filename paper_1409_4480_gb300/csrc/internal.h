@@ -20,6 +20,7 @@ struct GridDev {
   int n[3] = {0, 0, 0};
   int64_t stride[3] = {1, 0, 0};
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  float hf[3] = {0, 0, 0};             // h in FP32 (fill_f32)
   int periodic_xy = 0;
   int64_t n_cells = 0;
   // octree (kind == 1)
@@ -55,6 +56,14 @@ enum Counter {
 // per-launch diagnostic counters
 enum LaunchCounter { kCellVisits = 0, kPeelVisits, kPeelRays, kNumLaunchCounters };
 
+// FP32 copies of the run parameters that the FP32 path reads per event and
+// per peel-off ray: a double -> float conversion issues on the FP64 pipe,
+// which GB300 runs at 1/64 of the FP32 rate.
+struct RunF {
+  float tau_max = 50.f, albedo = 0.f, cam_scale = 1.f, cam_lo = 0.f, cam_hi = 1.f, cam_inv_width = 1.f,
+        fov_half = 1.f, pix_scale = 0.5f;
+};
+
 struct RunDev {
   uint64_t n_packets = 0;
   uint64_t pid_offset = 0;    // packet ids are pid_offset + [0, n_packets)
@@ -77,8 +86,33 @@ struct RunDev {
   double fov_half = 1.0;
   double pix_scale = 0.5;      // 1 / (2 fov_half)
   double centre[3] = {0, 0, 0};
+  RunF f;
   Tallies t;
 };
+
+// Host: refresh the FP32 copies after the double fields are set.
+inline void fill_f32(GridDev& g) {
+  for (int a = 0; a < 3; ++a) g.hf[a] = (float)g.h[a];
+}
+inline void fill_f32(RunDev& r) {
+  r.f.tau_max = (float)r.tau_max;
+  r.f.albedo = (float)r.albedo;
+  r.f.cam_scale = (float)r.cam_scale;
+  r.f.cam_lo = (float)r.cam_lo;
+  r.f.cam_hi = (float)r.cam_hi;
+  r.f.cam_inv_width = (float)r.cam_inv_width;
+  r.f.fov_half = (float)r.fov_half;
+  r.f.pix_scale = (float)r.pix_scale;
+}
+
+// A parameter in the transport precision R: the double field in the FP64
+// path, its FP32 copy in the FP32 path.
+template <typename R>
+__device__ __forceinline__ R prm(double d, float f);
+template <>
+__device__ __forceinline__ float prm<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double prm<double>(double d, float) { return d; }
 
 // One solve inside a launch: its grid, its parameters and its tallies.
 struct Job {

@@ -112,6 +112,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
       G.lo[a] = gv.lo[a];
       G.hi[a] = gv.hi[a];
       G.h[a] = (gv.hi[a] - gv.lo[a]) / G.n[a];
+      G.hf[a] = (float)G.h[a];
     }
     G.periodic_xy = gv.periodic_xy ? 1 : 0;
     G.n_cells = (int64_t)gv.nx * gv.ny * gv.nz;
@@ -154,6 +155,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     }
     r.fov_half = p.fov_half > 0 ? p.fov_half : fov;
     r.pix_scale = 0.5 / r.fov_half;
+    fill_f32(r);
     r.t.spec = t.spec;
     r.t.counters = t.counters;
     r.t.cam_spec = t.cam_spec;

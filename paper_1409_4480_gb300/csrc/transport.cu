@@ -145,9 +145,9 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     const int np = P.cam[cam].npix;
     if (np > 0 && P.t.cam_image) {
       const int au = (ax + 1) % 3, av = (ax + 2) % 3;
-      const R pix = R(P.pix_scale) * R(np);         // pixels per cm
-      const R fu = (R(s) * e.rel[au] + R(P.fov_half)) * pix;
-      const R fv = (e.rel[av] + R(P.fov_half)) * pix;
+      const R pix = prm<R>(P.pix_scale, P.f.pix_scale) * R(np);         // pixels per cm
+      const R fu = (R(s) * e.rel[au] + prm<R>(P.fov_half, P.f.fov_half)) * pix;
+      const R fv = (e.rel[av] + prm<R>(P.fov_half, P.f.fov_half)) * pix;
       if (fu >= R(0) && fu < R(np) && fv >= R(0) && fv < R(np)) {
         const int64_t iu = (int64_t)floor(fu), iv = (int64_t)floor(fv);
         atomicAdd(P.t.cam_image + P.cam[cam].img_off + (iv * np + iu) * P.cam_nb + bin, w);
@@ -191,7 +191,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     for (int a = 0; a < 3; ++a) {
       e.ijk[a] = ci[a];
       e.xi[a] = xi[a];
-      e.rel[a] = (R(ci[a]) + xi[a] - R(0.5) * R(G.n[a])) * R(G.h[a]);
+      e.rel[a] = (R(ci[a]) + xi[a] - R(0.5) * R(G.n[a])) * prm<R>(G.h[a], G.hf[a]);
       e.k[a] = kin ? kin[a] : R(0);
       e.ua[a] = ua ? ua[a] : R(0);
     }
@@ -327,7 +327,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       R hh[3], ik[3], kh[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        hh[a] = R(G.h[a]);
+        hh[a] = prm<R>(G.h[a], G.hf[a]);
         ik[a] = k[a] != R(0) ? R(1) / k[a] : R(0);
         kh[a] = k[a] / hh[a];
       }
@@ -404,7 +404,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         bool cont = true;
         if (b0.v[0] * ktot < R(r0.z)) {
           // dust: absorb with probability 1 - A, else isotropic scattering
-          if (b0.v[1] >= R(P.albedo)) {
+          if (b0.v[1] >= prm<R>(P.albedo, P.f.albedo)) {
             finish(2, 0.0);
             cont = false;
           } else {
@@ -509,11 +509,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           const R us = s > 0 ? e.u[ax] : -e.u[ax];
           // lab-frame Doppler velocity (km/s), invariant along the ray
           Vr = (xc + us) / e.inv_vth;
-          bin = bin_of_r<R>(Vr * R(P.cam_scale), R(P.cam_lo), R(P.cam_hi), R(P.cam_inv_width), P.cam_nb);
+          bin = bin_of_r<R>(Vr * prm<R>(P.cam_scale, P.f.cam_scale), prm<R>(P.cam_lo, P.f.cam_lo), prm<R>(P.cam_hi, P.f.cam_hi), prm<R>(P.cam_inv_width, P.f.cam_inv_width), P.cam_nb);
           if (bin < 0) {
             act = false;
           } else {
-            const R hax = R(G.h[ax]);
+            const R hax = prm<R>(G.h[ax], G.hf[ax]);
             const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
             lc[kPeelRays]++;
             lc[kPeelVisits]++;
@@ -522,7 +522,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             remaining = (s > 0 ? G.n[ax] - start : start + 1) - 1;
             step = (int64_t)s * G.stride[ax];
             cellp = e.cell + step;
-            if (tau_acc <= R(P.tau_max)) {
+            if (tau_acc <= prm<R>(P.tau_max, P.f.tau_max)) {
               const float4* __restrict__ rec = G.rec;
               for (int j = 0; j < kLanePeel && remaining > 0; ++j) {
                 const float4 q0 = __ldg(rec + 2 * cellp);
@@ -532,10 +532,10 @@ k_transport(const LaunchDev* __restrict__ Lp) {
                 lc[kPeelVisits]++;
                 cellp += step;
                 --remaining;
-                if (tau_acc > R(P.tau_max)) break;
+                if (tau_acc > prm<R>(P.tau_max, P.f.tau_max)) break;
               }
             }
-            if (tau_acc > R(P.tau_max)) {
+            if (tau_acc > prm<R>(P.tau_max, P.f.tau_max)) {
               act = false;
             } else if (remaining == 0) {
               peel_tally(P, e, cam, ax, s, bin, W * m_exp(-R(tau_acc)));
@@ -553,11 +553,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           const int axs = __shfl_sync(kFull, ax, own);
           const int ss = __shfl_sync(kFull, s, own);
           const R vv = __shfl_sync(kFull, Vr, own);
-          double tacc = (double)__shfl_sync(kFull, tau_acc, own);
+          R tacc = __shfl_sync(kFull, tau_acc, own);
           const Job* JS = L.jobs + __shfl_sync(kFull, e.job, own);
           const float4* __restrict__ rec = JS->g.rec;
-          const R hs = R(JS->g.h[axs]);
-          const double tmax = JS->p.tau_max;
+          const R hs = prm<R>(JS->g.h[axs], JS->g.hf[axs]);
+          const R tmax = prm<R>(JS->p.tau_max, JS->p.f.tau_max);
           bool cut = false;
           for (int base = 0; base < rem; base += 32) {
             const int m = base + lane;
@@ -572,10 +572,10 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tc += __shfl_xor_sync(kFull, tc, o);
-            tacc += (double)__shfl_sync(kFull, tc, 0);
+            tacc += __shfl_sync(kFull, tc, 0);
             if (tacc > tmax) { cut = true; break; }
           }
-          if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, W * m_exp(-R(tacc)));
+          if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, W * m_exp(-tacc));
         }
       }
     }
