@@ -111,6 +111,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_transport_sphere128_tau1e6_static_cap2000.md")
+KERNEL_SOURCES = ("paper_1409_4480_gb300/csrc/transport.cu", "paper_1409_4480_gb300/csrc/device.cuh",
+                  "paper_1409_4480_gb300/csrc/internal.h")
+
+
+def dram_bytes_per_scattering():
+    """DRAM bytes (read + write) per scattering of the transport kernel from the
+    committed ncu summary, or None when the kernel sources changed since that
+    capture (their sha256 is recorded in the summary)."""
+    import hashlib
+    import re
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    m_hash = re.search(r"kernel_source_sha256: `([0-9a-f]+)`", text)
+    m_val = re.search(r"dram_bytes_per_unit: ([0-9.eE+-]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != h.hexdigest():
+        return None
+    return float(m_val.group(1))
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -306,6 +332,8 @@ def run_gpu(args):
     fp32_peak = info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12
     per_scat = ((args.flops_peel * visits[1] + args.flops_cell * visits[0]) / max(plain_scat, 1)) + args.flops_scat
     achieved = per_scat * tot_scat / (ms / 1e3) / 1e12
+    dpb = dram_bytes_per_scattering()
+    traffic = dpb * plain_scat if dpb is not None else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
@@ -332,7 +360,9 @@ def run_gpu(args):
                        "plain_step": {"scatterings": plain_scat, "cell_visits": visits[0], "peel_visits": visits[1],
                                       "peel_rays": visits[2]}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None,
+                         "frac": achieved / fp32_peak, "traffic": traffic,
+                         "traffic_unit": "DRAM bytes per step (one launch of the 9 solves), ncu bytes per "
+                                         "scattering of the committed capture x scatterings per step",
                          "flops_per_scattering": per_scat,
                          "peak_source": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz "
                                         f"(max SM clock, of measured)"},
