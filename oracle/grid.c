@@ -192,16 +192,20 @@ int64_t o_locate_cell(const o_grid* g, const double r[3], const double k[3]) {
     if (r[a] == blo[a] && k[a] < 0.0) return -1;
     if (r[a] == bhi[a] && !(k[a] < 0.0)) return -1;
   }
+  /* the split plane of a node at depth d is lo + (2i + 1) s_d (i: the node's
+   * integer coordinate), the same number o_cell_bounds gives the leaf faces
+   * lying in it, so a point snapped onto a face is classified exactly */
   int64_t node = 0;
   int depth = 0;
+  int64_t ii[3] = {0, 0, 0};
   while (g->node_leaf[node] < 0) {
     int ci = 0;
     ++depth;
     for (int a = 0; a < 3; ++a) {
       double s = ldexp(g->hi[a] - g->lo[a], -depth);
-      double mid = blo[a] + s;
+      double mid = g->lo[a] + (double)(2 * ii[a] + 1) * s;
       int up = upper_side(r[a], mid, k[a]);
-      if (up) blo[a] = mid; else bhi[a] = mid;
+      ii[a] = 2 * ii[a] + up;
       ci |= up << a;
     }
     node = g->child[8 * node + ci];

@@ -175,3 +175,156 @@ def random_fields(shape, seed: int, lo=-PC_CM, hi=PC_CM, n_range=(1e-2, 10.0), T
                 vx=rng.normal(0, v_kms, m).astype(np.float32), vy=rng.normal(0, v_kms, m).astype(np.float32),
                 vz=rng.normal(0, v_kms, m).astype(np.float32),
                 k_dust=rng.uniform(0, k_dust_max, m).astype(np.float32), shape=(nx, ny, nz))
+
+
+# ------------------------------------------------------------------ octrees --
+def octree_refine(lo, hi, refine, min_level: int, max_level: int):
+    """Leaves of an octree over the box [lo, hi).
+
+    Starts from every node of the uniform level min_level and splits each node
+    for which refine(centre (m, 3), size (m, 3), level) is true, down to
+    max_level.  Returns (leaf_level uint8 (n,), leaf_ijk uint32 (n, 3)); leaf i
+    spans lo + ijk (hi - lo) 2^-level .. lo + (ijk + 1) (hi - lo) 2^-level, and
+    the leaves tile the box.  Order: level by level, x fastest within a level."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    n0 = 1 << min_level
+    kk, jj, ii = np.meshgrid(np.arange(n0), np.arange(n0), np.arange(n0), indexing="ij")
+    ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.int64)
+    offs = np.array([[(c >> 0) & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.int64)
+    levels, leaves = [], []
+    for L in range(min_level, max_level + 1):
+        size = (hi - lo) / float(1 << L)
+        if L < max_level and len(ijk):
+            split = np.asarray(refine(lo + (ijk + 0.5) * size, np.broadcast_to(size, ijk.shape), L), bool)
+        else:
+            split = np.zeros(len(ijk), bool)
+        keep = ijk[~split]
+        levels.append(np.full(len(keep), L, np.uint8))
+        leaves.append(keep)
+        ijk = (2 * ijk[split][:, None, :] + offs[None, :, :]).reshape(-1, 3)
+        if not len(ijk):
+            break
+    return np.concatenate(levels), np.concatenate(leaves).astype(np.uint32)
+
+
+def leaf_geometry(lo, hi, leaf_level, leaf_ijk):
+    """Centres and sizes (n, 3) of octree leaves."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    size = (hi - lo)[None, :] / np.exp2(leaf_level.astype(np.float64))[:, None]
+    return lo[None, :] + (leaf_ijk.astype(np.float64) + 0.5) * size, size
+
+
+def octree_grid(lo, hi, leaf_level, leaf_ijk, fields) -> Grid:
+    """Octree Grid from leaves and a dict of per-leaf fields (n_HI, T, vx,
+    vy, vz, k_dust; missing velocities and dust are zero)."""
+    n = len(leaf_level)
+    z = np.zeros(n, np.float32)
+    f32 = lambda k: np.asarray(fields[k], np.float32) if k in fields else z
+    return Grid(kind=KIND_OCTREE, lo=np.asarray(lo, np.float64), hi=np.asarray(hi, np.float64),
+                n_HI=f32("n_HI"), T=f32("T"), vx=f32("vx"), vy=f32("vy"), vz=f32("vz"), k_dust=f32("k_dust"),
+                leaf_level=np.ascontiguousarray(leaf_level, np.uint8),
+                leaf_ijk=np.ascontiguousarray(leaf_ijk, np.uint32).reshape(-1, 3))
+
+
+def octree_from_cartesian(g: Grid, seed: Optional[int] = None) -> Grid:
+    """The same cells as a Cartesian 2^L cube, stored as octree leaves of
+    level L (optionally in a seeded random leaf order)."""
+    nx, ny, nz = g.shape
+    L = int(round(math.log2(nx)))
+    if not (nx == ny == nz == 1 << L) or g.periodic_xy:
+        raise ValueError("needs an open 2^L cube")
+    c = np.arange(g.n_cells)
+    ijk = np.stack([c % nx, (c // nx) % ny, c // (nx * ny)], axis=1).astype(np.uint32)
+    order = np.random.default_rng(seed).permutation(g.n_cells) if seed is not None else c
+    fields = {k: getattr(g, k)[order] for k in ("n_HI", "T", "vx", "vy", "vz", "k_dust")}
+    out = octree_grid(g.lo, g.hi, np.full(g.n_cells, L, np.uint8)[order], ijk[order], fields)
+    out.meta = dict(g.meta, octree_of="cartesian", level=L, order_seed=seed)
+    return out
+
+
+def octree_sphere(T: float, tau0: float, R: float = PC_CM, v_max_kms: float = 0.0, tau_dust: float = 0.0,
+                  min_level: int = 3, max_level: int = 6) -> Grid:
+    """The uniform sphere of sphere() on an octree refined to max_level where a
+    leaf straddles the sphere surface (|r_centre - R| < leaf diagonal), and
+    kept at min_level elsewhere; fields at leaf centres as in sphere()."""
+    lo, hi = np.array([-R] * 3), np.array([R] * 3)
+
+    def refine(c, s, L):
+        return np.abs(np.linalg.norm(c, axis=1) - R) < np.linalg.norm(s, axis=1)
+
+    lv, ijk = octree_refine(lo, hi, refine, min_level, max_level)
+    c, _ = leaf_geometry(lo, hi, lv, ijk)
+    r = np.linalg.norm(c, axis=1)
+    inside = r < R
+    vs = np.where(inside, v_max_kms / R, 0.0)
+    g = octree_grid(lo, hi, lv, ijk, dict(
+        n_HI=np.where(inside, tau0 / (sigma0_recipe(T) * R), 0.0), T=np.full(len(lv), T),
+        vx=vs * c[:, 0], vy=vs * c[:, 1], vz=vs * c[:, 2], k_dust=np.where(inside, tau_dust / R, 0.0)))
+    g.meta = dict(model="octree_sphere", T=T, tau0=tau0, R=R, v_max_kms=v_max_kms, tau_dust=tau_dust,
+                  min_level=min_level, max_level=max_level)
+    return g
+
+
+MSUN_G = 1.98847e33
+M_P_G = 1.67262192e-24
+
+
+def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, conc: float = 5.0,
+         f_baryon: float = 0.157, x_h: float = 0.76, cone_half_angle_deg: float = 30.0,
+         clump_sigma: float = 1.0, turb_kms: float = 10.0, min_level: int = 6, max_level: int = 12,
+         cone_level: int = 9, leaf_mass_frac: float = 3e-6) -> Grid:
+    """Synthetic first-galaxy halo on an octree (stand-in for the paper's AMR
+    halo, whose simulation data are not available).
+
+    Box +-2 r_vir.  Gas: f_baryon times an NFW profile of mass m_vir inside
+    r_vir and concentration conc (rho(r) ~ 1 / ((r/r_s)(1 + r/r_s)^2),
+    r_s = r_vir / conc), hydrogen mass fraction x_h, taken at the leaf centre
+    (at least half a leaf size from the centre).  Inside a bicone of half angle
+    cone_half_angle_deg about z: T = 1e4 K and x_HI = 1e-4; outside: T = 100 K,
+    neutral.  Clumping: each leaf's density times exp(sigma G - sigma^2/2),
+    G ~ N(0, 1) per leaf (mean preserving).  Turbulence: independent Gaussian
+    velocity of turb_kms per component per leaf.  No dust.
+    Refinement: a node splits while its gas mass exceeds leaf_mass_frac of the
+    gas mass inside r_vir (down to max_level), or while it straddles the cone
+    surface inside r_vir (down to cone_level), starting from min_level."""
+    rng = np.random.default_rng(seed)
+    R = 2.0 * r_vir
+    lo, hi = np.array([-R] * 3), np.array([R] * 3)
+    r_s = r_vir / conc
+    m_c = math.log(1.0 + conc) - conc / (1.0 + conc)
+    rho_s = m_vir_msun * MSUN_G / (4.0 * math.pi * r_s ** 3 * m_c)
+    m_gas = f_baryon * m_vir_msun * MSUN_G
+    cos_cone = math.cos(math.radians(cone_half_angle_deg))
+
+    def rho_gas(c, s):
+        r = np.maximum(np.linalg.norm(c, axis=1), 0.5 * s[:, 0])
+        q = r / r_s
+        return f_baryon * rho_s / (q * (1.0 + q) ** 2)
+
+    def refine(c, s, L):
+        mass = rho_gas(c, s) * s[:, 0] * s[:, 1] * s[:, 2]
+        r = np.linalg.norm(c, axis=1)
+        half_diag = 0.5 * np.linalg.norm(s, axis=1)
+        # straddles the cone surface |z| = r cos(theta_c): the surface passes within the leaf
+        dist = np.abs(np.abs(c[:, 2]) * math.sin(math.acos(cos_cone))
+                      - np.hypot(c[:, 0], c[:, 1]) * cos_cone)
+        return (mass > leaf_mass_frac * m_gas) | ((dist < half_diag) & (r < r_vir) & (L < cone_level))
+
+    lv, ijk = octree_refine(lo, hi, refine, min_level, max_level)
+    c, s = leaf_geometry(lo, hi, lv, ijk)
+    n = len(lv)
+    r = np.linalg.norm(c, axis=1)
+    in_cone = np.abs(c[:, 2]) > cos_cone * r
+    clump = np.exp(clump_sigma * rng.standard_normal(n) - 0.5 * clump_sigma ** 2)
+    n_h = x_h * rho_gas(c, s) * clump / M_P_G
+    x_hi = np.where(in_cone, 1e-4, 1.0)
+    g = octree_grid(lo, hi, lv, ijk, dict(
+        n_HI=n_h * x_hi, T=np.where(in_cone, 1e4, 100.0),
+        vx=rng.normal(0.0, turb_kms, n), vy=rng.normal(0.0, turb_kms, n), vz=rng.normal(0.0, turb_kms, n)))
+    g.meta = dict(model="halo", seed=seed, r_vir=r_vir, m_vir_msun=m_vir_msun, conc=conc, f_baryon=f_baryon,
+                  cone_half_angle_deg=cone_half_angle_deg, clump_sigma=clump_sigma, turb_kms=turb_kms,
+                  min_level=min_level, max_level=max_level, cone_level=cone_level, leaf_mass_frac=leaf_mass_frac,
+                  n_leaves=n)
+    return g
