@@ -19,7 +19,9 @@
  *     root box; a leaf spans lo + ijk s_L .. lo + (ijk+1) s_L, s_L = (hi-lo) 2^-L;
  *     crossing into an octree leaf locates the face point from the root.
  * Non-local estimate readings: paths run along the six coordinate axes from
- * the centre of each face of the cell outward; the density reference is the
+ * the centre of each face of the cell outward (on octrees a centre lying on a
+ * finer neighbour's split plane enters its upper side, the direction tie
+ * rule for a zero direction component); the density reference is the
  * cell itself; a path continues while |n_i - n_ref| < f_NL n_ref and stops at
  * the domain edge (a periodic axis is followed for at most one period); the
  * path sum is sum a_i k_HI,i l_i with l_i the leaf length along the path.
@@ -287,7 +289,15 @@ static void atau_nl_range(o_grid* g, double f_nl, int64_t c0, int64_t c1) {
       double k[3] = {0.0, 0.0, 0.0};
       k[ax] = (dir & 1) ? -1.0 : 1.0;
       double r[3];
-      for (int a = 0; a < 3; ++a) r[a] = 0.5 * (clo[a] + chi[a]);
+      for (int a = 0; a < 3; ++a) {
+        /* the centre of an octree leaf is the split plane of its level L + 1,
+         * lo + (2i + 1) s_{L+1}, taken as that same number: where a finer
+         * neighbour is split there, the path enters its upper side */
+        if (g->kind == 1)
+          r[a] = g->lo[a] + (double)(2 * (int64_t)g->ijk[3 * c + a] + 1) * ldexp(g->hi[a] - g->lo[a], -(g->lev[c] + 1));
+        else
+          r[a] = 0.5 * (clo[a] + chi[a]);
+      }
       int64_t cur = c;
       double sum = 0.0;
       int64_t steps = 0;

@@ -20,6 +20,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "colt.h"
@@ -43,6 +44,8 @@ double now_ms() {
 struct GridObj {
   GridDev dev;
   float4* rec = nullptr;
+  int32_t* node = nullptr;              // octree: node table (device)
+  uint32_t* nbr = nullptr;              // octree: face neighbours (device)
   size_t bytes = 0;
   // longest history (scatterings) any finished solve on this grid has had
   uint64_t longest = 0;
@@ -78,7 +81,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   bool in_flight = false;
   std::vector<std::pair<uint64_t, uint64_t>> jobs;  // (request id, packets)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][grid kind]
 };
 
 struct Tally {
@@ -334,37 +337,38 @@ int ensure_slot(colt_ctx* ctx, int si) {
 // Enqueue one persistent launch over the jobs staged in the slot's host
 // buffer: header/job-table copy, counter reset, kernel.  Recorded once per
 // (slot, precision) as a CUDA graph and replayed.
-int enqueue_launch(colt_ctx* ctx, int si, int precision, int blocks_per_sm) {
+int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_per_sm) {
   Slot& sl = ctx->slots[si];
   LaunchBuf& lb = sl.lb;
   const int gi = precision == COLT_PLAIN ? 0 : 1;
+  const int gk = kind == COLT_OCTREE ? 1 : 0;
   ++ctx->launches;
   if (blocks_per_sm > 0) {
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
     CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
-    CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, blocks_per_sm, ctx->sm_count,
+    CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, blocks_per_sm, ctx->sm_count,
                         sl.stream));
     CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
   }
-  if (!sl.graph[gi]) {
+  if (!sl.graph[gi][gk]) {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
     cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
-    cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, 0, ctx->sm_count,
+    cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, 0, ctx->sm_count,
                                       sl.stream);
     cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                     cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "transport launch (capture)");
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
-    cudaError_t ie = cudaGraphInstantiate(&sl.graph[gi], g, 0);
+    cudaError_t ie = cudaGraphInstantiate(&sl.graph[gi][gk], g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
   }
-  CU(cudaGraphLaunch(sl.graph[gi], sl.stream));
+  CU(cudaGraphLaunch(sl.graph[gi][gk], sl.stream));
   return COLT_OK;
 }
 
@@ -415,12 +419,85 @@ int copy_result(colt_ctx* ctx, const colt_run_params* p, const Tally& t, colt_re
   return COLT_OK;
 }
 
+// Octree tables from the leaves (host): node[v] >= 0 is the first of v's 8
+// children, node[v] < 0 marks leaf -1 - node[v]; the leaves must tile the box
+// (every internal node has 8 children, no leaf overlaps another).
+constexpr int32_t kUnset = INT32_MIN;
+
+int build_octree_tables(colt_ctx* ctx, int64_t n, const uint8_t* lev, const uint32_t* ijk,
+                        std::vector<int32_t>* node_out, std::vector<uint32_t>* nbr_out, int* max_level) {
+  std::vector<int32_t>& node = *node_out;
+  node.assign(1, kUnset);
+  int maxl = 0;
+  for (int64_t l = 0; l < n; ++l) {
+    const int L = lev[l];
+    if (L > kMaxOctLevel) return fail(ctx, COLT_EINVAL, "octree level above the supported maximum");
+    maxl = std::max(maxl, L);
+    for (int a = 0; a < 3; ++a)
+      if ((uint64_t)ijk[3 * l + a] >= (1ull << L)) return fail(ctx, COLT_EINVAL, "leaf coordinate outside its level");
+    size_t v = 0;
+    for (int t = 1; t <= L; ++t) {
+      if (node[v] != kUnset && node[v] < 0) return fail(ctx, COLT_EINVAL, "octree leaves overlap");
+      if (node[v] == kUnset) {
+        if (node.size() + 8 > (size_t)kNodeMask) return fail(ctx, COLT_EINVAL, "octree has too many nodes");
+        node[v] = (int32_t)node.size();
+        node.resize(node.size() + 8, kUnset);
+      }
+      int cidx = 0;
+      for (int a = 0; a < 3; ++a) cidx |= (int)((ijk[3 * l + a] >> (L - t)) & 1u) << a;
+      v = (size_t)node[v] + cidx;
+    }
+    if (node[v] != kUnset) return fail(ctx, COLT_EINVAL, "octree leaves overlap");
+    node[v] = -1 - (int32_t)l;
+  }
+  for (int32_t v : node)
+    if (v == kUnset) return fail(ctx, COLT_EINVAL, "octree leaves do not tile the box");
+  // face neighbours: the node across each face at the leaf's level, or the
+  // coarser leaf that covers it
+  std::vector<uint32_t>& nbr = *nbr_out;
+  nbr.assign(6 * (size_t)n, kNoNbr);
+  auto work = [&](int64_t l0, int64_t l1) {
+    for (int64_t l = l0; l < l1; ++l) {
+      const int L = lev[l];
+      for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1;
+        int64_t adj[3] = {ijk[3 * l], ijk[3 * l + 1], ijk[3 * l + 2]};
+        adj[ax] += (f & 1) ? -1 : 1;
+        if (adj[ax] < 0 || adj[ax] >= (int64_t)1 << L) continue;
+        size_t v = 0;
+        int t = 0;
+        while (t < L && node[v] >= 0) {
+          ++t;
+          int cidx = 0;
+          for (int a = 0; a < 3; ++a) cidx |= (int)((adj[a] >> (L - t)) & 1) << a;
+          v = (size_t)node[v] + cidx;
+        }
+        nbr[6 * l + f] = (uint32_t)v | ((uint32_t)t << 27);
+      }
+    }
+  };
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(16, n / 65536));
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(work, n * i / nt, n * (i + 1) / nt);
+  for (auto& t : th) t.join();
+  *max_level = maxl;
+  return COLT_OK;
+}
+
 int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
   if (!d) return fail(ctx, COLT_EINVAL, "desc is NULL");
-  if (d->kind != COLT_CARTESIAN) return fail(ctx, COLT_EINVAL, "octree grids are not supported by this build");
-  if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(ctx, COLT_EINVAL, "cell counts must be positive");
-  const int64_t n = (int64_t)d->nx * d->ny * d->nz;
-  if (n > (int64_t)1 << 31) return fail(ctx, COLT_EINVAL, "too many cells");
+  const bool oct = d->kind == COLT_OCTREE;
+  if (!oct && d->kind != COLT_CARTESIAN) return fail(ctx, COLT_EINVAL, "unknown grid kind");
+  int64_t n = 0;
+  if (oct) {
+    if (d->n_cells <= 0 || !d->leaf_level || !d->leaf_ijk) return fail(ctx, COLT_EINVAL, "octree needs leaves");
+    if (d->periodic_xy) return fail(ctx, COLT_EINVAL, "periodic boundaries need a Cartesian grid");
+    n = d->n_cells;
+  } else {
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(ctx, COLT_EINVAL, "cell counts must be positive");
+    n = (int64_t)d->nx * d->ny * d->nz;
+  }
+  if (n >= ((int64_t)1 << 31) - 1) return fail(ctx, COLT_EINVAL, "too many cells");
   for (int a = 0; a < 3; ++a)
     if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->lo[a]) || !std::isfinite(d->hi[a]))
       return fail(ctx, COLT_EINVAL, "box must have hi > lo");
@@ -441,7 +518,14 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
     }
   }
   CU(cudaStreamSynchronize(ctx->stream));
-  const size_t bytes = sizeof(float4) * 2 * (size_t)n;
+  std::vector<int32_t> node;
+  std::vector<uint32_t> nbr;
+  int max_level = 0;
+  if (oct) {
+    int rc = build_octree_tables(ctx, n, d->leaf_level, d->leaf_ijk, &node, &nbr, &max_level);
+    if (rc) return rc;
+  }
+  const size_t bytes = sizeof(float4) * 2 * (size_t)n + sizeof(int32_t) * node.size() + sizeof(uint32_t) * nbr.size();
   if (ctx->used + bytes > ctx->budget) return fail(ctx, COLT_ENOMEM, "grid exceeds the memory budget");
   std::vector<float4> rec(2 * (size_t)n);
   for (int64_t c = 0; c < n; ++c) {
@@ -455,25 +539,49 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
     rec[2 * c + 1] = make_float4((float)(f[2][c] / vth), (float)(f[3][c] / vth), (float)(f[4][c] / vth), 0.0f);
   }
   GridDev& G = g->dev;
-  G.kind = COLT_CARTESIAN;
-  G.n[0] = d->nx; G.n[1] = d->ny; G.n[2] = d->nz;
-  G.stride[0] = 1; G.stride[1] = d->nx; G.stride[2] = (int64_t)d->nx * d->ny;
+  G.kind = oct ? COLT_OCTREE : COLT_CARTESIAN;
+  if (!oct) {
+    G.n[0] = d->nx; G.n[1] = d->ny; G.n[2] = d->nz;
+    G.stride[0] = 1; G.stride[1] = d->nx; G.stride[2] = (int64_t)d->nx * d->ny;
+  }
   for (int a = 0; a < 3; ++a) {
     G.lo[a] = d->lo[a];
     G.hi[a] = d->hi[a];
-    G.h[a] = (d->hi[a] - d->lo[a]) / G.n[a];
-    G.hf[a] = (float)G.h[a];
+    G.h[a] = oct ? (d->hi[a] - d->lo[a]) : (d->hi[a] - d->lo[a]) / G.n[a];
   }
-  G.periodic_xy = d->periodic_xy ? 1 : 0;
+  fill_f32(G);
+  G.periodic_xy = (!oct && d->periodic_xy) ? 1 : 0;
   G.n_cells = n;
-  CU(cudaMalloc(&g->rec, bytes));
-  CU(cudaMemcpyAsync(g->rec, rec.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+  G.max_level = max_level;
+  CU(cudaMalloc(&g->rec, sizeof(float4) * 2 * (size_t)n));
+  CU(cudaMemcpyAsync(g->rec, rec.data(), sizeof(float4) * 2 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
   G.rec = g->rec;
+  if (oct) {
+    CU(cudaMalloc(&g->node, sizeof(int32_t) * node.size()));
+    CU(cudaMalloc(&g->nbr, sizeof(uint32_t) * nbr.size()));
+    CU(cudaMemcpyAsync(g->node, node.data(), sizeof(int32_t) * node.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(g->nbr, nbr.data(), sizeof(uint32_t) * nbr.size(), cudaMemcpyHostToDevice, ctx->stream));
+    G.node = g->node;
+    G.nbr = g->nbr;
+  }
   // non-local a tau (Eq. atauNL), once per grid
   float* dn = nullptr;
   CU(cudaMallocAsync(&dn, sizeof(float) * n, ctx->stream));
   CU(cudaMemcpyAsync(dn, f[0], sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
-  cudaError_t e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->stream);
+  cudaError_t e = cudaSuccess;
+  if (oct) {
+    uint8_t* dlev = nullptr;
+    uint32_t* dijk = nullptr;
+    CU(cudaMallocAsync(&dlev, (size_t)n, ctx->stream));
+    CU(cudaMallocAsync(&dijk, sizeof(uint32_t) * 3 * (size_t)n, ctx->stream));
+    CU(cudaMemcpyAsync(dlev, d->leaf_level, (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dijk, d->leaf_ijk, sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+    e = launch_atau_nl_oct(G, dn, dlev, dijk, d->f_nl, g->rec, ctx->stream);
+    cudaFreeAsync(dlev, ctx->stream);
+    cudaFreeAsync(dijk, ctx->stream);
+  } else {
+    e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->stream);
+  }
   cudaFreeAsync(dn, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "atau_nl kernel");
@@ -482,7 +590,15 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
   return COLT_OK;
 }
 
-// ----------------------------------------------------------- serving core --
+void free_grid(GridObj& g) {
+  if (g.rec) cudaFree(g.rec);
+  if (g.node) cudaFree(g.node);
+  if (g.nbr) cudaFree(g.nbr);
+  g.rec = nullptr;
+  g.node = nullptr;
+  g.nbr = nullptr;
+}
+
 // Record the longest history a finished job saw on its grid.
 void learn_cost(colt_ctx* ctx, colt_grid grid, uint64_t longest) {
   auto g = ctx->grids.find(grid);
@@ -581,10 +697,16 @@ int serve_launch(colt_ctx* ctx, int si) {
     }
     return a->id < b->id;
   });
+  // all jobs of a launch share one precision and one grid kind
+  auto kind_of = [&](const Req* r) {
+    auto g = ctx->grids.find(r->grid);
+    return g == ctx->grids.end() ? COLT_CARTESIAN : g->second.dev.kind;
+  };
   const int prec = act.front()->p.precision;
+  const int kind = kind_of(act.front());
   std::vector<Req*> sel;
   for (Req* r : act)
-    if (r->p.precision == prec && (int)sel.size() < kMaxJobs) sel.push_back(r);
+    if (r->p.precision == prec && kind_of(r) == kind && (int)sel.size() < kMaxJobs) sel.push_back(r);
   int rc = ensure_slot(ctx, si);
   if (rc) return rc;
   Slot& sl = ctx->slots[si];
@@ -623,7 +745,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   h->total = total;
   // tallies were allocated and zeroed on the context stream
   CU(cudaStreamWaitEvent(sl.stream, ctx->ev_alloc, 0));
-  rc = enqueue_launch(ctx, si, prec, 0);
+  rc = enqueue_launch(ctx, si, prec, kind, 0);
   if (rc) return rc;
   CU(cudaLaunchHostFunc(sl.stream, slot_done_cb, ctx));
   CU(cudaEventRecord(sl.done, sl.stream));
@@ -703,10 +825,11 @@ void colt_finalize(colt_ctx* ctx) {
       if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->reqs) free_tally(&kv.second->tally);
-    for (auto& kv : ctx->grids) cudaFree(kv.second.rec);
+    for (auto& kv : ctx->grids) free_grid(kv.second);
     cudaStreamSynchronize(ctx->stream);
     for (auto& sl : ctx->slots) {
-      for (auto& g : sl.graph) if (g) cudaGraphExecDestroy(g);
+      for (auto& gp : sl.graph)
+        for (auto& g : gp) if (g) cudaGraphExecDestroy(g);
       if (sl.lb.host) cudaFreeHost(sl.lb.host);
       if (sl.lb.dev) cudaFree(sl.lb.dev);
       if (sl.lb.work) cudaFree(sl.lb.work);
@@ -741,7 +864,8 @@ int colt_create_grid(colt_ctx* ctx, const colt_grid_desc* desc, colt_grid* out) 
   GridObj g;
   int rc = build_grid(ctx, desc, &g);
   if (rc) {
-    if (g.rec) cudaFree(g.rec);
+    cudaStreamSynchronize(ctx->stream);
+    free_grid(g);
     return rc;
   }
   const uint64_t h = ctx->next_handle++;
@@ -760,7 +884,7 @@ int colt_destroy_grid(colt_ctx* ctx, colt_grid grid) {
     if (kv.second->grid == grid && kv.second->state != kDone)
       return fail(ctx, COLT_EINVAL, "grid is in use by an unfinished request");
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(it->second.rec);
+  free_grid(it->second);
   ctx->used -= it->second.bytes;
   ctx->grids.erase(it);
   return COLT_OK;
@@ -784,6 +908,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   cudaSetDevice(ctx->device);
   const int prec = params[0].precision;
   std::vector<const GridObj*> gs(n);
+  int kind = COLT_CARTESIAN;
   for (int i = 0; i < n; ++i) {
     auto it = ctx->grids.find(grids[i]);
     if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
@@ -791,7 +916,9 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     int rc = validate_params(ctx, &params[i]);
     if (rc) return rc;
     if (params[i].precision != prec) return fail(ctx, COLT_EINVAL, "all solves of a batch need one precision");
+    if (gs[i]->dev.kind != gs[0]->dev.kind) return fail(ctx, COLT_EINVAL, "all solves of a batch need one grid kind");
   }
+  kind = gs[0]->dev.kind;
   // a blocking run waits for in-flight serving launches first
   int rc = drain_slots(ctx);
   if (rc) return rc;
@@ -830,7 +957,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   float ms = 0;
   if (total > 0) {
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
-    rc = enqueue_launch(ctx, 0, prec, params[0].blocks_per_sm);
+    rc = enqueue_launch(ctx, 0, prec, kind, params[0].blocks_per_sm);
     if (rc) { free_all(); return rc; }
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     CU(cudaMemcpyAsync(lcnt, lb.work + 1, sizeof(lcnt), cudaMemcpyDeviceToHost, ctx->stream));

@@ -14,20 +14,31 @@ constexpr int kMaxCams = 8;
 //   r0 = (k_HI = n_HI sigma_0 [1/cm], a, k_dust [1/cm], 1/v_th [s/km])
 //   r1 = (u_x, u_y, u_z [v/v_th], a tau_NL)
 // Cartesian cells are stored x-fastest; octree leaves in input order.
+// Octree (kind 1): leaf i of level L and integer coordinates ijk spans
+// lo + ijk h 2^-L .. lo + (ijk + 1) h 2^-L, h = hi - lo (the root size).
+//   node[v] >= 0 : v is internal, its 8 children are node[v] + (bx | by<<1 | bz<<2)
+//   node[v] <  0 : v is leaf -1 - node[v]
+//   nbr[6 i + 2 a + (0: +a face, 1: -a face)] = the node across that face at
+//     the leaf's level or the coarser leaf covering it, packed as
+//     id | level << 27; kNoNbr when the face is on the box boundary.
+constexpr uint32_t kNoNbr = 0xFFFFFFFFu;
+constexpr uint32_t kNodeMask = (1u << 27) - 1u;
+constexpr int kMaxOctLevel = 24;
+
 struct GridDev {
   const float4* rec = nullptr;
   int kind = 0;
   int n[3] = {0, 0, 0};
   int64_t stride[3] = {1, 0, 0};
+  // Cartesian: h = cell size; octree: h = root size (a leaf of level L: h 2^-L)
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, h[3] = {0, 0, 0};
   float hf[3] = {0, 0, 0};             // h in FP32 (fill_f32)
+  float halff[3] = {0, 0, 0};          // half the box size in FP32
   int periodic_xy = 0;
   int64_t n_cells = 0;
   // octree (kind == 1)
-  const int32_t* node = nullptr;       // per node: >= 0 first child, < 0 -> leaf (-1 - leaf)
-  const int32_t* nbr = nullptr;        // per leaf: 6 face neighbours (node ids, same or coarser), -1 = outside
-  const uint8_t* leaf_level = nullptr;
-  const uint32_t* leaf_ijk = nullptr;  // 3 per leaf
+  const int32_t* node = nullptr;
+  const uint32_t* nbr = nullptr;
   int max_level = 0;
 };
 
@@ -92,7 +103,10 @@ struct RunDev {
 
 // Host: refresh the FP32 copies after the double fields are set.
 inline void fill_f32(GridDev& g) {
-  for (int a = 0; a < 3; ++a) g.hf[a] = (float)g.h[a];
+  for (int a = 0; a < 3; ++a) {
+    g.hf[a] = (float)g.h[a];
+    g.halff[a] = (float)(0.5 * (g.hi[a] - g.lo[a]));
+  }
 }
 inline void fill_f32(RunDev& r) {
   r.f.tau_max = (float)r.tau_max;
@@ -135,11 +149,16 @@ struct LaunchDev {
 
 // launchers (transport.cu)
 // L is a DEVICE pointer to the launch header (so a captured graph can replay it).
-cudaError_t launch_transport(const LaunchDev* L, int precision, int blocks_per_sm, int sm_count, cudaStream_t s);
-// persistent grid size the launcher uses for a precision
-int transport_grid_size(int precision, int blocks_per_sm, int sm_count);
+// All jobs of a launch share one grid kind (COLT_CARTESIAN / COLT_OCTREE).
+cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int blocks_per_sm, int sm_count,
+                             cudaStream_t s);
+// persistent grid size the launcher uses for a precision and grid kind
+int transport_grid_size(int precision, int kind, int blocks_per_sm, int sm_count);
 // grid preparation (grid.cu)
 cudaError_t launch_atau_nl(const GridDev& g, const float* n_hi, double f_nl, float4* rec_mut, cudaStream_t s);
+// octree grids: lev / ijk are the device copies of the leaves' levels and coordinates
+cudaError_t launch_atau_nl_oct(const GridDev& g, const float* n_hi, const uint8_t* lev, const uint32_t* ijk,
+                               double f_nl, float4* rec_mut, cudaStream_t s);
 // parity helpers (parity.cu)
 cudaError_t launch_voigt(const void* a, const void* x, void* H, size_t n, int precision, cudaStream_t s);
 struct ScatterIODev;

@@ -112,8 +112,8 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
       G.lo[a] = gv.lo[a];
       G.hi[a] = gv.hi[a];
       G.h[a] = (gv.hi[a] - gv.lo[a]) / G.n[a];
-      G.hf[a] = (float)G.h[a];
     }
+    fill_f32(G);
     G.periodic_xy = gv.periodic_xy ? 1 : 0;
     G.n_cells = (int64_t)gv.nx * gv.ny * gv.nz;
     RunDev& r = jobs[i].p;
@@ -193,7 +193,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     return COLT_ECUDA;
   if (cudaMemcpyAsync(scratch, host, kOffJobs + sizeof(Job) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return COLT_ECUDA;
-  if (total > 0 && launch_transport(reinterpret_cast<const LaunchDev*>(scratch), precision,
+  if (total > 0 && launch_transport(reinterpret_cast<const LaunchDev*>(scratch), precision, COLT_CARTESIAN,
                                     params[0].blocks_per_sm, sm_count, stream) != cudaSuccess)
     return COLT_ECUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return COLT_ECUDA;

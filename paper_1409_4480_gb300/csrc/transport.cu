@@ -26,6 +26,7 @@
 #include <cstdio>
 
 #include "internal.h"
+#include "octree.cuh"
 
 namespace colt {
 
@@ -42,8 +43,10 @@ struct PeelEv {
   R rel[3];     // event position relative to the box centre (cm), for image pixels
   int64_t cell;
   int ijk[3];
+  int lvl;      // octree leaf level (0 on Cartesian grids)
   int job;
-  R xi[3];
+  R xi[3];      // position in the event cell (cell units)
+  R xt[3];      // 1 - xi, formed from the exact position
   R x;          // comoving frequency at the event (before the scattering)
   R k[3];       // incoming direction (HI scattering)
   R ua[3];      // atom velocity (HI scattering)
@@ -112,7 +115,7 @@ __device__ __forceinline__ int64_t cell_index(const GridDev& G, const int c3[3])
   return (int64_t)c3[0] + G.stride[1] * c3[1] + G.stride[2] * c3[2];
 }
 
-template <typename R, int kWarps>
+template <typename R, int kWarps, bool kOct>
 __global__ void __launch_bounds__(kWarps * 32)
 k_transport(const LaunchDev* __restrict__ Lp) {
   const LaunchDev L = *Lp;
@@ -129,7 +132,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   uint64_t pid = 0;
   uint32_t event = 0, nscat = 0, nscat_hi = 0;
   int ci[3] = {0, 0, 0};
-  R xi[3] = {0, 0, 0};
+  int lvl = 0;            // octree leaf level
+  int64_t leaf = 0;       // octree leaf index
+  CellPos<R> xi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xi[a].set(R(0));
   R k[3] = {0, 0, 1};
   R x = 0;
   TauLeft<R> tau;
@@ -187,15 +194,18 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     PeelEv<R>& e = sev[lane];
     e.type = type;
     e.job = jb;
+    const R lsc = kOct ? pow2neg<R>(lvl) : R(1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       e.ijk[a] = ci[a];
-      e.xi[a] = xi[a];
-      e.rel[a] = (R(ci[a]) + xi[a] - R(0.5) * R(G.n[a])) * prm<R>(G.h[a], G.hf[a]);
+      e.xi[a] = xi[a].val();
+      e.xt[a] = xi[a].from_top();
+      e.rel[a] = (R(ci[a]) + e.xi[a]) * (prm<R>(G.h[a], G.hf[a]) * lsc) - prm<R>(0.5 * (G.hi[a] - G.lo[a]), G.halff[a]);
       e.k[a] = kin ? kin[a] : R(0);
       e.ua[a] = ua ? ua[a] : R(0);
     }
-    e.cell = cell_index(G, ci);
+    e.lvl = lvl;
+    e.cell = kOct ? leaf : cell_index(G, ci);
     e.x = xin;
     e.upar = upar;
     e.g = g;
@@ -283,28 +293,66 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             r[2] += P.src_sigma * rho2 * c2;
           }
           bool inside = true;
+          if constexpr (kOct) {
+            // descend from the root, split planes lo + (2i + 1) h 2^-d
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const double t = (r[a] - G.lo[a]) / G.h[a];
-            const double f = floor(t);
-            int i = 0;
-            R loc = R(0);
-            const bool in_range = f >= -1.0 && f <= (double)G.n[a];
-            if (in_range) {
-              i = (int)f;
-              loc = R(t - f);
-              if (t == f && k[a] < R(0)) { i -= 1; loc = R(1); }
+            for (int a = 0; a < 3; ++a) {
+              if (!(r[a] >= G.lo[a] && r[a] <= G.hi[a]) || (r[a] == G.lo[a] && k[a] < R(0)) ||
+                  (r[a] == G.hi[a] && !(k[a] < R(0))))
+                inside = false;
+              ci[a] = 0;
             }
-            if (!in_range || i < 0 || i >= G.n[a]) { inside = false; i = 0; }
-            ci[a] = i;
-            xi[a] = loc;
+            lvl = 0;
+            if (inside) {
+              int32_t ch;
+              uint32_t v = 0;
+              while ((ch = __ldg(G.node + v)) >= 0 && lvl < kMaxOctLevel) {
+                ++lvl;
+                int cidx = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  // rounded product, then rounded sum (no fused multiply-add):
+                  // the same number as the leaf faces lying in this plane
+                  const double mid =
+                      __dadd_rn(G.lo[a], __dmul_rn((double)(2 * ci[a] + 1), G.h[a] * pow2neg<double>(lvl)));
+                  const int up = (r[a] > mid) || (r[a] == mid && !(k[a] < R(0)));
+                  ci[a] = 2 * ci[a] + up;
+                  cidx |= up << a;
+                }
+                v = (uint32_t)ch + (uint32_t)cidx;
+              }
+              leaf = -1 - (int64_t)__ldg(G.node + v);
+              if (leaf < 0 || leaf >= G.n_cells) { atomicExch(L.error, 1); inside = false; leaf = 0; }
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const double hl = G.h[a] * pow2neg<double>(lvl);
+                xi[a].set_d((r[a] - __dadd_rn(G.lo[a], __dmul_rn((double)ci[a], hl))) / hl);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const double t = (r[a] - G.lo[a]) / G.h[a];
+              const double f = floor(t);
+              int i = 0;
+              double loc = 0.0;
+              const bool in_range = f >= -1.0 && f <= (double)G.n[a];
+              if (in_range) {
+                i = (int)f;
+                loc = t - f;
+                if (t == f && k[a] < R(0)) { i -= 1; loc = 1.0; }
+              }
+              if (!in_range || i < 0 || i >= G.n[a]) { inside = false; i = 0; }
+              ci[a] = i;
+              xi[a].set_d(loc);
+            }
           }
           x = R(0);
           alive = true;
           if (!inside) {
             finish(1, 0.0);     // source outside the box: leaves at line centre
           } else if (P.n_cam > 0) {
-            const int64_t c = cell_index(G, ci);
+            const int64_t c = kOct ? leaf : cell_index(G, ci);
             fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, __ldg(G.rec + 2 * c), __ldg(G.rec + 2 * c + 1));
             has_peel = true;
           }
@@ -324,14 +372,25 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       const float4* __restrict__ rec = G.rec;
       const uint64_t rpid = pid + P.pid_offset;
       // per flight: cell size, inverse direction, direction in cell units
-      R hh[3], ik[3], kh[3];
+      // (octree: of a root-sized cell, scaled by 2^-level at each crossing)
+      R hh[3], ik[3], kh[3], h0[3], kh0[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        hh[a] = prm<R>(G.h[a], G.hf[a]);
+        h0[a] = prm<R>(G.h[a], G.hf[a]);
         ik[a] = k[a] != R(0) ? R(1) / k[a] : R(0);
-        kh[a] = k[a] / hh[a];
+        kh0[a] = k[a] / h0[a];
+        hh[a] = h0[a];
+        kh[a] = kh0[a];
       }
-      int64_t c = cell_index(G, ci);
+      if constexpr (kOct) {
+        const R sc = pow2neg<R>(lvl);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          hh[a] = h0[a] * sc;
+          kh[a] = kh0[a] / sc;
+        }
+      }
+      int64_t c = kOct ? leaf : cell_index(G, ci);
       float4 r0 = __ldg(rec + 2 * c), r1 = __ldg(rec + 2 * c + 1);
       R ktot = 0;
       bool interact = false, escaped = false;
@@ -347,7 +406,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (k[a] != R(0)) {
-            R d = (k[a] > R(0) ? (R(1) - xi[a]) : -xi[a]) * hh[a] * ik[a];
+            R d = (k[a] > R(0) ? xi[a].from_top() : -xi[a].val()) * hh[a] * ik[a];
             if (d < R(0)) d = R(0);
             if (d < tmin) { tmin = d; ax = a; }
           }
@@ -355,28 +414,47 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         if (tau.reached(ktot * tmin)) {
           const R le = tau.value() / ktot;
 #pragma unroll
-          for (int a = 0; a < 3; ++a) xi[a] += le * kh[a];
+          for (int a = 0; a < 3; ++a) xi[a].add(le * kh[a]);
           interact = true;
           break;
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) if (a != ax) xi[a] += tmin * kh[a];
+        for (int a = 0; a < 3; ++a) if (a != ax) xi[a].add(tmin * kh[a]);
         // cross the face on axis ax
         const int sgn = k[ax] > R(0) ? 1 : -1;
-        int ni = ci[ax] + sgn;
-        xi[ax] = sgn > 0 ? R(0) : R(1);
-        if (ni < 0 || ni >= G.n[ax]) {
-          if (G.periodic_xy && ax < 2) {
-            ni = ni < 0 ? G.n[ax] - 1 : 0;
-          } else {
+        if constexpr (kOct) {
+          xi[ax].set(sgn > 0 ? R(1) : R(0));
+          const int lvl_old = lvl;
+          const int64_t nl = oct_cross<R>(G, c, ax, sgn, k, ci, &lvl, xi);
+          if (nl < 0) {
             escaped = true;
             break;
           }
+          leaf = nl;
+          if (lvl != lvl_old) {
+            const R sc = pow2neg<R>(lvl);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              hh[a] = h0[a] * sc;
+              kh[a] = kh0[a] / sc;
+            }
+          }
+        } else {
+          int ni = ci[ax] + sgn;
+          xi[ax].set(sgn > 0 ? R(0) : R(1));
+          if (ni < 0 || ni >= G.n[ax]) {
+            if (G.periodic_xy && ax < 2) {
+              ni = ni < 0 ? G.n[ax] - 1 : 0;
+            } else {
+              escaped = true;
+              break;
+            }
+          }
+          ci[ax] = ni;
         }
-        ci[ax] = ni;
         const R ku_old = k[0] * R(r1.x) + k[1] * R(r1.y) + k[2] * R(r1.z);
         const R ivth_old = R(r0.w);
-        c = cell_index(G, ci);
+        c = kOct ? leaf : cell_index(G, ci);
         if (c < 0 || c >= G.n_cells) { atomicExch(L.error, 1); status = 3; break; }
         r0 = __ldg(rec + 2 * c);
         r1 = __ldg(rec + 2 * c + 1);
@@ -424,7 +502,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           if (P.core_skip) {
             R lmin = R(3.0e38);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) lmin = fmin(lmin, fmin(xi[q], R(1) - xi[q]) * hh[q]);
+            for (int q = 0; q < 3; ++q) lmin = fmin(lmin, fmin(xi[q].val(), xi[q].from_top()) * hh[q]);
             lmin = fmax(lmin, R(0));
             atau0 = a * R(r0.x) * lmin + R(r1.w);
           }
@@ -513,11 +591,39 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           if (bin < 0) {
             act = false;
           } else {
-            const R hax = prm<R>(G.h[ax], G.hf[ax]);
-            const R l0 = (s > 0 ? (R(1) - e.xi[ax]) : e.xi[ax]) * hax;
+            const R hax = prm<R>(G.h[ax], G.hf[ax]) * (kOct ? pow2neg<R>(e.lvl) : R(1));
+            const R l0 = (s > 0 ? e.xt[ax] : e.xi[ax]) * hax;
             lc[kPeelRays]++;
             lc[kPeelVisits]++;
             tau_acc = (e.kHI * voigt<R>(e.a, xc) + e.kd) * l0;
+            if constexpr (kOct) {
+              // octree: this lane walks the ray leaf by leaf to the cutoff or
+              // the box edge (the next leaf depends on the last one)
+              const float4* __restrict__ rec = G.rec;
+              const R tmax = prm<R>(P.tau_max, P.f.tau_max);
+              const R h0ax = prm<R>(G.h[ax], G.hf[ax]);
+              R kr[3] = {R(0), R(0), R(0)};
+              kr[ax] = R(s);
+              int cj[3] = {e.ijk[0], e.ijk[1], e.ijk[2]};
+              CellPos<R> xj[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) xj[a].set(e.xi[a]);
+              int lv = e.lvl;
+              int64_t cur = e.cell;
+              for (uint32_t guard = 0; tau_acc <= tmax && guard < kMaxFlightVisits; ++guard) {
+                xj[ax].set(s > 0 ? R(1) : R(0));
+                const int64_t nx = oct_cross<R>(G, cur, ax, s, kr, cj, &lv, xj);
+                if (nx < 0) break;
+                if (nx >= G.n_cells) { atomicExch(L.error, 1); tau_acc = R(3.0e38); break; }
+                const float4 q0 = __ldg(rec + 2 * nx);
+                const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * nx + 1) + ax);
+                const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
+                tau_acc += (R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * (h0ax * pow2neg<R>(lv));
+                lc[kPeelVisits]++;
+                cur = nx;
+              }
+              remaining = 0;
+            } else {
             const int start = e.ijk[ax];
             remaining = (s > 0 ? G.n[ax] - start : start + 1) - 1;
             step = (int64_t)s * G.stride[ax];
@@ -534,6 +640,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
                 --remaining;
                 if (tau_acc > prm<R>(P.tau_max, P.f.tau_max)) break;
               }
+            }
             }
             if (tau_acc > prm<R>(P.tau_max, P.f.tau_max)) {
               act = false;
@@ -605,11 +712,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #undef COLT_MARK
 }
 
-template <typename R>
+template <typename R, bool kOct>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
   constexpr int kWarps = 8;
   const size_t smem = sizeof(PeelEv<R>) * 32 * kWarps;
-  auto kern = k_transport<R, kWarps>;
+  auto kern = k_transport<R, kWarps, kOct>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -621,26 +728,33 @@ static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_transport(const LaunchDev* L, int precision, int blocks_per_sm, int sm_count, cudaStream_t s) {
-  if (precision == 0) return launch_t<double>(L, blocks_per_sm, sm_count, s);
-  return launch_t<float>(L, blocks_per_sm, sm_count, s);
+cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int blocks_per_sm, int sm_count,
+                             cudaStream_t s) {
+  if (kind == 1) {
+    if (precision == 0) return launch_t<double, true>(L, blocks_per_sm, sm_count, s);
+    return launch_t<float, true>(L, blocks_per_sm, sm_count, s);
+  }
+  if (precision == 0) return launch_t<double, false>(L, blocks_per_sm, sm_count, s);
+  return launch_t<float, false>(L, blocks_per_sm, sm_count, s);
 }
 
-}  // namespace colt
-
-namespace colt {
-int transport_grid_size(int precision, int blocks_per_sm, int sm_count) {
+template <typename R, bool kOct>
+static int grid_size_t(int blocks_per_sm, int sm_count) {
   constexpr int kWarps = 8;
   int occ = 0;
-  if (precision == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<double, kWarps>, kWarps * 32,
-                                                  sizeof(PeelEv<double>) * 32 * kWarps);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<float, kWarps>, kWarps * 32,
-                                                  sizeof(PeelEv<float>) * 32 * kWarps);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<R, kWarps, kOct>, kWarps * 32,
+                                                sizeof(PeelEv<R>) * 32 * kWarps);
   if (occ < 1) occ = 1;
   if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
   return occ * sm_count;
 }
+
+int transport_grid_size(int precision, int kind, int blocks_per_sm, int sm_count) {
+  if (kind == 1)
+    return precision == 0 ? grid_size_t<double, true>(blocks_per_sm, sm_count)
+                          : grid_size_t<float, true>(blocks_per_sm, sm_count);
+  return precision == 0 ? grid_size_t<double, false>(blocks_per_sm, sm_count)
+                        : grid_size_t<float, false>(blocks_per_sm, sm_count);
+}
+
 }  // namespace colt
