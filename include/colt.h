@@ -70,10 +70,12 @@ int colt_device_info(colt_ctx* ctx, int* sm_count, size_t* l2_bytes, int* cc_maj
  * temperature and bulk velocity per cell, plus grey dust opacity.
  *   Cartesian: nx*ny*nz cells, x fastest, spanning the box [lo, hi).
  *   Octree: n_cells leaves; leaf i has refinement level leaf_level[i] (0 =
- *   root) and integer coordinates leaf_ijk[3i..3i+2] at that level, i.e. it
- *   spans lo + ijk (hi-lo) 2^-level .. lo + (ijk+1) (hi-lo) 2^-level.  The
- *   leaves must tile the box exactly (checked: COLT_EINVAL otherwise).
- *   leaf_level / leaf_ijk are host arrays.
+ *   root, at most 24) and integer coordinates leaf_ijk[3i..3i+2] at that
+ *   level, i.e. it spans lo + ijk (hi-lo) 2^-level .. lo + (ijk+1) (hi-lo)
+ *   2^-level.  The leaves must tile the box exactly, with fewer than 2^27 tree
+ *   nodes (checked: COLT_EINVAL otherwise).  leaf_level / leaf_ijk are host
+ *   arrays; the library builds a node table and per-leaf face neighbours
+ *   (4 + 24 bytes per leaf beside the 32-byte record).
  * Field arrays (n_cells FP32 each) are host or device memory per fields_mem;
  * k_dust may be NULL (no dust).  T must be > 0 everywhere (empty cells carry
  * any positive temperature).
@@ -179,8 +181,10 @@ int colt_run(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_resul
 
 /* Blocking batched solve: n (1..256) independent solves -- each with its own
  * grid, parameters and results (arrays of n) -- share one persistent launch,
- * so short and long solves fill the GPU together.  params[i].precision must
- * be equal for all i.  out[i].kernel_ms is the shared launch's time. */
+ * so short and long solves fill the GPU together.  params[i].precision and
+ * the grid kind (Cartesian / octree) must be equal for all i (COLT_EINVAL).
+ * The launch starts the solves whose grids have shown the longest histories
+ * first.  out[i].kernel_ms is the shared launch's time. */
 int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
                    colt_result* out);
 
@@ -191,7 +195,9 @@ int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params*
 /* ------------------------------------------------------------- serving -- */
 /* Continuous batching.  colt_submit enqueues a solve (non-blocking); requests
  * are admitted as memory (mem_budget_bytes) and batch slots free up, and the
- * packets of all admitted requests share persistent launches.  Returns
+ * packets of all admitted requests share persistent launches (up to three in
+ * flight; each launch holds requests of one precision and one grid kind,
+ * longest expected histories first, a request passed over four times first).  Returns
  * COLT_EAGAIN when the request cannot be queued now (queue full).  The grid
  * must stay alive until the request is released.  Results of a request are
  * identical to colt_run of the same (grid, params) up to floating-point
