@@ -328,3 +328,89 @@ def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, c
                   min_level=min_level, max_level=max_level, cone_level=cone_level, leaf_mass_frac=leaf_mass_frac,
                   n_leaves=n)
     return g
+
+
+def _trilinear(field: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Periodic trilinear interpolation of field[z, y, x] at fractional grid
+    coordinates u (m, 3) = (x, y, z) in units of the grid spacing (cell centres
+    at integer + 0.5)."""
+    n = field.shape[0]
+    g = u - 0.5
+    i0 = np.floor(g).astype(np.int64)
+    f = g - i0
+    out = np.zeros(len(u))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                w = (f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) * (f[:, 2] if dz else 1 - f[:, 2])
+                out += w * field[(i0[:, 2] + dz) % n, (i0[:, 1] + dy) % n, (i0[:, 0] + dx) % n]
+    return out
+
+
+def cosmo_box(seed: int = 5, n_fft: int = 256, box_cmpc: float = 1.0, z: float = 10.0, sigma_g: float = 2.0,
+              slope: float = -2.5, min_level: int = 7, max_level: int = 14, leaf_mass_frac: float = 4e-7,
+              n_sources: int = 5):
+    """Synthetic cosmological volume on an octree (stand-in for the paper's
+    1 Mpc^3 post-processing box, whose simulation is not available).
+
+    A Gaussian field G with power spectrum P(k) ~ k^slope is drawn on an
+    n_fft^3 periodic FFT grid (seeded), scaled to standard deviation sigma_g,
+    and turned into the lognormal overdensity 1 + delta = exp(G - sigma_g^2/2).
+    The box is box_cmpc comoving Mpc at redshift z (physical side
+    box / (1 + z)).  Hydrogen density n_H = 1.9e-7 (1 + z)^3 (1 + delta) cm^-3.
+    Stated relations: T = 200 K (1 + delta)^0.6 clipped to [10, 1e5] K;
+    x_HI = (1 + delta) / (1 + delta + 0.1).  Peculiar velocities from the linear
+    continuity relation on the Gaussian field, v_k = i a H f G_k k / k^2 (k
+    comoving; = i H f G_k q / q^2 with q = k / a the physical wavenumber),
+    f = 1, H(z) = 70 km/s/Mpc sqrt(0.3 (1+z)^3 + 0.7).  Fields are
+    interpolated trilinearly to leaf centres.  No dust.
+    Refinement: from the uniform level min_level, a leaf splits while its
+    hydrogen mass exceeds leaf_mass_frac of the box's, down to max_level.
+    Returns (grid, sources): the n_sources highest-overdensity points of the
+    FFT grid (cell centres, cm, box-centred), highest first."""
+    rng = np.random.default_rng(seed)
+    L = box_cmpc * 3.0856775814913673e24 / (1.0 + z)        # physical side, cm
+    half = 0.5 * L
+    k1 = np.fft.fftfreq(n_fft) * n_fft
+    kz, ky, kx = np.meshgrid(k1, k1, k1[: n_fft // 2 + 1], indexing="ij")
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    amp = np.power(k2, slope / 4.0)
+    amp[0, 0, 0] = 0.0
+    noise = rng.standard_normal((n_fft, n_fft, n_fft))
+    gk = np.fft.rfftn(noise) * amp
+    G = np.fft.irfftn(gk, s=(n_fft,) * 3)
+    scale = sigma_g / G.std()
+    G *= scale
+    gk *= scale
+    one_delta = np.exp(G - 0.5 * sigma_g ** 2)
+    hz = 70.0 * math.sqrt(0.3 * (1.0 + z) ** 3 + 0.7) / 3.0856775814913673e19   # 1/s
+    qphys = 2.0 * math.pi / L                                                    # per grid wavenumber, 1/cm
+    vel = []
+    for kc in (kx, ky, kz):
+        vk = 1j * hz * gk * (kc * qphys) / (k2 * qphys * qphys)
+        vk[0, 0, 0] = 0.0
+        vel.append(np.fft.irfftn(vk, s=(n_fft,) * 3) / 1e5)                     # km/s
+    lo, hi = np.array([-half] * 3), np.array([half] * 3)
+    nh_mean = 1.9e-7 * (1.0 + z) ** 3
+    m_box = nh_mean * L ** 3
+
+    def refine(c, s, lev):
+        u = (c - lo) / (hi - lo) * n_fft
+        return nh_mean * _trilinear(one_delta, u) * s[:, 0] * s[:, 1] * s[:, 2] > leaf_mass_frac * m_box
+
+    lv, ijk = octree_refine(lo, hi, refine, min_level, max_level)
+    c, _ = leaf_geometry(lo, hi, lv, ijk)
+    u = (c - lo) / (hi - lo) * n_fft
+    od = _trilinear(one_delta, u)
+    T = np.clip(200.0 * od ** 0.6, 10.0, 1e5)
+    x_hi = od / (od + 0.1)
+    g = octree_grid(lo, hi, lv, ijk, dict(n_HI=nh_mean * od * x_hi, T=T, vx=_trilinear(vel[2], u),
+                                          vy=_trilinear(vel[1], u), vz=_trilinear(vel[0], u)))
+    top = np.argsort(one_delta.ravel())[::-1][:n_sources]
+    iz, iy, ix = np.unravel_index(top, one_delta.shape)
+    src = np.stack([ix, iy, iz], axis=1) + 0.5
+    sources = [tuple(lo + s / n_fft * (hi - lo)) for s in src]
+    g.meta = dict(model="cosmo_box", seed=seed, n_fft=n_fft, box_cmpc=box_cmpc, z=z, sigma_g=sigma_g, slope=slope,
+                  min_level=min_level, max_level=max_level, leaf_mass_frac=leaf_mass_frac, n_leaves=len(lv))
+    return g, sources
