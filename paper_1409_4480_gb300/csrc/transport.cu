@@ -51,7 +51,8 @@ struct PeelEv {
   R k[3];       // incoming direction (HI scattering)
   R ua[3];      // atom velocity (HI scattering)
   R upar, g, RQ;
-  R inv_vth, u[3];
+  R vth, wn;    // the cell's v_th (km/s) and the phase weight's normaliser 1 / (1 + RQ/3)
+  R u[3];
   R kHI, a, kd; // the event cell's opacity record (first cell of every peel-off ray)
   int type;     // 0: isotropic with W = 1 and x unchanged (emission, dust); 1: HI
 };
@@ -121,6 +122,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   const LaunchDev L = *Lp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PeelEv<R>* sev = reinterpret_cast<PeelEv<R>*>(smem_raw) + (threadIdx.x >> 5) * 32;
+  // lanes of the warp's events in ballot order (peel-off pair -> event)
+  int* sidx = reinterpret_cast<int*>(smem_raw + sizeof(PeelEv<R>) * 32 * kWarps) + (threadIdx.x >> 5) * 32;
   const int lane = threadIdx.x & 31;
 
   unsigned long long lc[kNumLaunchCounters] = {0, 0, 0};
@@ -210,7 +213,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     e.upar = upar;
     e.g = g;
     e.RQ = RQ;
-    e.inv_vth = r0.w;
+    e.vth = R(1) / R(r0.w);
+    e.wn = R(1) / (R(1) + RQ / R(3));
     e.u[0] = r1.x; e.u[1] = r1.y; e.u[2] = r1.z;
     e.kHI = r0.x;
     e.a = r0.y;
@@ -553,14 +557,18 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       const int ncl = has_peel ? L.jobs[sev[lane].job].p.n_cam : 0;
       const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncl);
       const int n_pairs = __popc(pm) * ncam_max;
+      if (has_peel) sidx[__popc(pm & ((1u << lane) - 1u))] = lane;
+      __syncwarp();
+      // q / ncam_max for q < 2^20, ncam_max <= 8: (q + 1/2) / n lies >= 1/16 from an integer
+      const float inv_nc = n_pairs ? 1.0f / (float)ncam_max : 0.0f;
       for (int pbase = 0; pbase < n_pairs; pbase += 32) {
         const int q = pbase + lane;
         bool act = q < n_pairs;
         int src = __ffs(pm) - 1, cam = 0;
         if (act) {
-          const int k = q / ncam_max;
+          const int k = (int)(((float)q + 0.5f) * inv_nc);
           cam = q - k * ncam_max;
-          src = (int)__fns(pm, 0, k + 1);
+          src = sidx[k];
         }
         const PeelEv<R>& e = sev[src];
         const Job* JE = L.jobs + e.job;
@@ -580,13 +588,13 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           R xc = e.x;
           if (e.type == 1) {
             const R mu_c = s > 0 ? e.k[ax] : -e.k[ax];
-            W = (R(1) + e.RQ * mu_c * mu_c) / (R(1) + e.RQ / R(3));
+            W = (R(1) + e.RQ * mu_c * mu_c) * e.wn;
             const R kcu = s > 0 ? e.ua[ax] : -e.ua[ax];
             xc = e.x + kcu - e.upar + e.g * (mu_c - R(1));
           }
           const R us = s > 0 ? e.u[ax] : -e.u[ax];
           // lab-frame Doppler velocity (km/s), invariant along the ray
-          Vr = (xc + us) / e.inv_vth;
+          Vr = (xc + us) * e.vth;
           bin = bin_of_r<R>(Vr * prm<R>(P.cam_scale, P.f.cam_scale), prm<R>(P.cam_lo, P.f.cam_lo), prm<R>(P.cam_hi, P.f.cam_hi), prm<R>(P.cam_inv_width, P.f.cam_inv_width), P.cam_nb);
           if (bin < 0) {
             act = false;
@@ -715,7 +723,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 template <typename R, bool kOct>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
   constexpr int kWarps = 8;
-  const size_t smem = sizeof(PeelEv<R>) * 32 * kWarps;
+  const size_t smem = (sizeof(PeelEv<R>) + sizeof(int)) * 32 * kWarps;
   auto kern = k_transport<R, kWarps, kOct>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -743,7 +751,7 @@ static int grid_size_t(int blocks_per_sm, int sm_count) {
   constexpr int kWarps = 8;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<R, kWarps, kOct>, kWarps * 32,
-                                                sizeof(PeelEv<R>) * 32 * kWarps);
+                                                (sizeof(PeelEv<R>) + sizeof(int)) * 32 * kWarps);
   if (occ < 1) occ = 1;
   if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
   return occ * sm_count;
