@@ -142,14 +142,17 @@ __device__ __forceinline__ R x_crit_of(R atau0) {
 // ---------------------------------------------------------------- u_par --
 // Sec. 3.2.3.  Draws for |x|, sign restored at the end.  Trial t uses Philox
 // block 2 + t of the event; the caller passes block 2 (computed alongside the
-// event's other blocks).  The proposal angle is carried as psi = theta + pi/2
-// in (0, pi), so that tan(theta) = -cos(psi)/sin(psi) is well conditioned near
-// theta = +-pi/2 in FP32:
-//   |x| <= 1        : psi = pi R
-//   lower piece     : psi = alpha R,                 alpha = theta0 + pi/2
-//   upper piece     : psi = alpha + (pi - alpha) R
-// with alpha = atan2(a, |x| - u0) and p = alpha / ((1 - e0) alpha + e0 pi),
-// algebraically the paper's theta0 and p.
+// event's other blocks).  The proposal angle is carried in units of pi as
+// w = (theta + pi/2) / pi in (0, 1), so that tan(theta) = -cos(pi w)/sin(pi w)
+// is well conditioned near theta = +-pi/2 in FP32 (sincospi is exact in its
+// argument's scaling):
+//   |x| <= 1        : w = R1                               (accept R2 < e^{-u^2})
+//   lower piece     : w = alpha' R2                        (accept R3 < e^{-u^2})
+//   upper piece     : w = alpha' + (1 - alpha') R2         (accept R3 < e^{u0^2-u^2})
+// with alpha' = atan2(a, |x| - u0) / pi and p = alpha' / ((1 - e0) alpha' + e0),
+// algebraically the paper's theta0 and p.  The |x| <= 1 regime is the lower
+// piece with alpha' = 1, its draws taken from the slots the paper's order
+// gives it (angle R1, acceptance R2), so both regimes share one trial loop.
 template <typename R>
 __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64_t pid, uint32_t event,
                                          const U4<R>& first, int* n_trials) {
@@ -160,47 +163,40 @@ __device__ __forceinline__ R sample_upar(R x, R a, R xcw, const Rng& rng, uint64
     m_sincospi(R(2) * first.v[1], &s, &c);
     u = m_div(R(1), xa) + m_sqrt(-m_log(first.v[0])) * c;
     *n_trials = 1;
-  } else if (xa <= R(1)) {
-    int t = 0;
-    U4<R> q = first;
-    for (;;) {
-      if (t >= kMaxTrials) { *n_trials = kMaxTrials + 1; break; }
-      if (t > 0) q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
-      ++t;
-      R s, c;
-      m_sincospi(q.v[0], &s, &c);
-      u = xa - m_div(a * c, s);
-      if (q.v[1] < m_exp(-u * u)) { *n_trials = t; break; }
-    }
   } else {
-    // d = |x| - u0 taken straight from the two u0 forms (u0_core = x - 1/(x +
-    // e^{1-x^2}/a), u0_wing = x_cw - 1/x_cw + 0.15 (x - x_cw)): forming it as
-    // |x| - u0 would cancel (d ~ a near |x| = 1) and cost FP32 its accuracy
-    const R d = (xa < xcw) ? m_div(R(1), xa + m_div(m_exp(R(1) - xa * xa), a))
-                           : R(0.85) * (xa - xcw) + m_div(R(1), xcw);
-    const R u0 = xa - d;
-    const R alpha = m_atan2(a, d);
-    const R e0 = m_exp(-u0 * u0);
-    const R p = m_div(alpha, (R(1) - e0) * alpha + e0 * R(kPi));
+    const bool small = xa <= R(1);
+    R d = R(0), ap = R(1), p = R(2);   // |x| <= 1: never the upper piece
+    if (!small) {
+      // d = |x| - u0 taken straight from the two u0 forms (u0_core = x - 1/(x +
+      // e^{1-x^2}/a), u0_wing = x_cw - 1/x_cw + 0.15 (x - x_cw)): forming it as
+      // |x| - u0 would cancel (d ~ a near |x| = 1) and cost FP32 its accuracy
+      d = (xa < xcw) ? m_div(R(1), xa + m_div(m_exp(R(1) - xa * xa), a))
+                     : R(0.85) * (xa - xcw) + m_div(R(1), xcw);
+      const R u0 = xa - d;
+      ap = m_atan2(a, d) * R(1.0 / kPi);
+      const R e0 = m_exp(-u0 * u0);
+      p = m_div(ap, (R(1) - e0) * ap + e0);
+    }
     int t = 0;
     U4<R> q = first;
     for (;;) {
       if (t >= kMaxTrials) { *n_trials = kMaxTrials + 1; break; }
       if (t > 0) q = uniforms<R>(rng, pid, event, 2u + uint32_t(t));
       ++t;
+      const R ra = small ? q.v[0] : q.v[1];     // angle draw
+      const R rc = small ? q.v[1] : q.v[2];     // acceptance draw
       const bool upper = p < q.v[0];
-      // psi = alpha R on the lower piece, alpha + (pi - alpha) R on the upper;
-      // past pi/2 the upper piece uses the exact complement
-      // pi - psi = (pi - alpha)(1 - R), so that sin stays well conditioned
-      const R psi = upper ? m_fma(R(kPi) - alpha, q.v[1], alpha) : alpha * q.v[1];
-      const bool flip = upper && psi > R(0.5 * kPi);
+      // upper piece past w = 1/2: the exact complement 1 - w = (1 - alpha')(1 - R)
+      // keeps sin(pi w) well conditioned
+      const R w = upper ? m_fma(R(1) - ap, ra, ap) : ap * ra;
+      const bool flip = upper && w > R(0.5);
       R s, c;
-      m_sincos(flip ? (R(kPi) - alpha) * (R(1) - q.v[1]) : psi, &s, &c);
+      m_sincospi(flip ? (R(1) - ap) * (R(1) - ra) : w, &s, &c);
       const R tt = flip ? -m_div(a * c, s) : m_div(a * c, s);   // |x| - u
       u = xa - tt;
       // upper piece: exp(u0^2 - u^2) with u0 - u = tt - d, u0 + u = 2|x| - d - tt
       const R acc = upper ? m_exp((tt - d) * (R(2) * xa - d - tt)) : m_exp(-u * u);
-      if (q.v[2] < acc) { *n_trials = t; break; }
+      if (rc < acc) { *n_trials = t; break; }
     }
   }
   return x < R(0) ? -u : u;
