@@ -59,16 +59,6 @@ struct GridObj {
 // has never run sorts first.
 uint64_t grid_cost(const GridObj& g) { return g.measured ? g.longest : ~0ull; }
 
-// Isolation threshold of the kernel's refill (see k_transport): half the
-// longest history seen on the grid, for grids whose histories are long
-// enough for a warp of their own to pay (otherwise never).
-#ifndef COLT_ISO_SHIFT
-#define COLT_ISO_SHIFT 1
-#endif
-uint32_t iso_of(const GridObj& g) {
-  if (!g.measured || g.longest < 40000) return 0xFFFFFFFFu;
-  return (uint32_t)std::min<uint64_t>(g.longest >> COLT_ISO_SHIFT, 0xFFFFFFFEu);
-}
 
 // Device + pinned staging for one persistent launch: header, job_end, jobs.
 struct LaunchBuf {
@@ -736,7 +726,6 @@ int serve_launch(colt_ctx* ctx, int si) {
     Job& J = lb.jobs_h()[nj];
     J.g = g.dev;
     J.p = r->run;
-    J.p.iso_scatter = iso_of(g);
     J.p.n_packets = take;
     J.p.pid_offset = r->run.pid_offset + r->next_local;
     total += take;
@@ -958,7 +947,6 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     Job& J = lb.jobs_h()[q];
     J.g = gs[i]->dev;
     J.p = make_run(*gs[i], &params[i]);
-    J.p.iso_scatter = iso_of(*gs[i]);
     attach_tally(&J.p, ts[i]);
     total += params[i].n_packets;
     lb.end_h()[q] = total;

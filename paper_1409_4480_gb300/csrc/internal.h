@@ -85,9 +85,6 @@ struct RunDev {
   double tau_max = 50.0;
   double albedo = 0.0;
   uint64_t max_scatter = ~0ull;
-  // a warp holding a packet past this many scatterings takes no new packets,
-  // so the long history runs in a nearly empty warp (~0: never)
-  uint32_t iso_scatter = 0xFFFFFFFFu;
   double spec_scale = 1.0;    // spectral coordinate = (lab Doppler velocity [km/s]) * scale
   double spec_lo = 0, spec_hi = 1;
   int spec_nb = 1;

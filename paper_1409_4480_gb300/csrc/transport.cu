@@ -253,13 +253,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   for (;;) {
     bool has_peel = false;
     // ---------------------------------------------------------- refill --
-    // Long-history isolation: packets are independent, but lanes of a warp share
-    // its instruction stream, so a long history sharing its warp with 31 busy
-    // lanes advances at the rate of a full warp.  While a warp holds a packet
-    // past its job's iso_scatter, its free lanes take no new packets; the warp
-    // drains to the long packet, which then runs at the latency of one lane.
-    const bool hold = __any_sync(kFull, alive && nscat > J->p.iso_scatter);
-    const unsigned need = hold ? 0u : __ballot_sync(kFull, !alive && !done);
+    const unsigned need = __ballot_sync(kFull, !alive && !done);
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
