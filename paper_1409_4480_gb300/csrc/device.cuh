@@ -208,9 +208,21 @@ template <typename R>
 __device__ __forceinline__ R sample_mu(R RQ, R u) {
   if (RQ == R(0)) return R(2) * u - R(1);
   const R c = (R(2) * u - R(1)) * (R(1) + RQ * R(1.0 / 3.0));
-  const R sp3 = m_sqrt(m_div(R(1), RQ));    // sqrt(p/3), p = 3/RQ; mu^3 + p mu - p c = 0
+  // sqrt(p/3) = sqrt(1/RQ), p = 3/RQ; mu^3 + p mu - p c = 0.  The two values
+  // R/Q takes (3/7 in the core, 1 in the wing) use constants.
+  R sp3, isp3;
+  if (RQ == R(1)) {
+    sp3 = R(1);
+    isp3 = R(1);
+  } else if (RQ == R(3.0 / 7.0)) {
+    sp3 = R(1.5275252316519468);     // sqrt(7/3)
+    isp3 = R(0.65465367070797714);   // sqrt(3/7)
+  } else {
+    sp3 = m_sqrt(m_div(R(1), RQ));
+    isp3 = m_div(R(1), sp3);
+  }
   // root = -2 sqrt(p/3) sinh( asinh( (3q/(2p)) sqrt(3/p) ) / 3 ),  3q/(2p) = -1.5 c
-  return R(2) * sp3 * m_sinh(m_asinh(m_div(R(1.5) * c, sp3)) * R(1.0 / 3.0));
+  return R(2) * sp3 * m_sinh(m_asinh(R(1.5) * c * isp3) * R(1.0 / 3.0));
 }
 
 // Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin (2017),
@@ -225,8 +237,9 @@ __device__ __forceinline__ void onb(const R n[3], R e1[3], R e2[3]) {
 }
 
 // One resonant scattering (Sec. 3.1.3 with Sec. 3.2.3-3.2.4).  The caller
-// passes the event's draw blocks 0 (word 3: core R/Q choice), 1 (u_perp R1,
-// R2, mu, phi) and 2 (first u_par trial); later trials draw blocks 3, 4, ...
+// passes x_cw of the cell's damping parameter (Eq. xcw, x_cw_fit) and the
+// event's draw blocks 0 (word 3: core R/Q choice), 1 (u_perp R1, R2, mu, phi)
+// and 2 (first u_par trial); later trials draw blocks 3, 4, ...
 // Returns outgoing direction, atom velocity and x_f.
 template <typename R>
 struct ScatterOut {
@@ -237,9 +250,8 @@ struct ScatterOut {
 template <typename R>
 __device__ __forceinline__ ScatterOut<R> scatter_hi(R x, const R k[3], R a, R g, R atau0, int phase,
                                                     const Rng& rng, uint64_t pid, uint32_t event,
-                                                    R core_choice, const U4<R>& b1, const U4<R>& b2) {
+                                                    R core_choice, const U4<R>& b1, const U4<R>& b2, R xcw) {
   ScatterOut<R> o;
-  const R xcw = x_cw_fit<R>(a);
   R xc = atau0 >= R(0) ? x_crit_of<R>(atau0) : R(0);
   if (fabs(x) >= xc) xc = R(0);
   o.x_crit = xc;

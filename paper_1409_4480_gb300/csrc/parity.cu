@@ -37,7 +37,7 @@ __global__ void k_scatter(colt_scatter_io* io, size_t n, Rng rng) {
   const U4<R> b1 = uniforms<R>(rng, v.pid, v.event, 1);
   const U4<R> b2 = uniforms<R>(rng, v.pid, v.event, 2);
   const ScatterOut<R> o = scatter_hi<R>(R(v.x), k, R(v.a), R(v.g), R(v.atau0), v.phase, rng, v.pid, v.event,
-                                        b0.v[3], b1, b2);
+                                        b0.v[3], b1, b2, x_cw_fit<R>(R(v.a)));
   v.x_f = o.x_f;
   for (int q = 0; q < 3; ++q) {
     v.k_f[q] = o.k_f[q];

@@ -124,6 +124,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   PeelEv<R>* sev = reinterpret_cast<PeelEv<R>*>(smem_raw) + (threadIdx.x >> 5) * 32;
   // lanes of the warp's events in ballot order (peel-off pair -> event)
   int* sidx = reinterpret_cast<int*>(smem_raw + sizeof(PeelEv<R>) * 32 * kWarps) + (threadIdx.x >> 5) * 32;
+  // per lane: the damping parameter of the last resonant scattering and its
+  // x_cw (Eq. xcw depends on the cell temperature only; a packet scatters
+  // many times in one cell)
+  R* sxcw = reinterpret_cast<R*>(smem_raw + (sizeof(PeelEv<R>) + sizeof(int)) * 32 * kWarps) + 2 * threadIdx.x;
+  sxcw[0] = R(-1);
   const int lane = threadIdx.x & 31;
 
   unsigned long long lc[kNumLaunchCounters] = {0, 0, 0};
@@ -213,8 +218,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     e.upar = upar;
     e.g = g;
     e.RQ = RQ;
-    e.vth = R(1) / R(r0.w);
-    e.wn = R(1) / (R(1) + RQ / R(3));
+    e.vth = m_div(R(1), R(r0.w));
+    e.wn = m_div(R(1), R(1) + RQ * R(1.0 / 3.0));
     e.u[0] = r1.x; e.u[1] = r1.y; e.u[2] = r1.z;
     e.kHI = r0.x;
     e.a = r0.y;
@@ -381,8 +386,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         h0[a] = prm<R>(G.h[a], G.hf[a]);
-        ik[a] = k[a] != R(0) ? R(1) / k[a] : R(0);
-        kh0[a] = k[a] / h0[a];
+        ik[a] = k[a] != R(0) ? m_div(R(1), k[a]) : R(0);
+        kh0[a] = m_div(k[a], h0[a]);
         hh[a] = h0[a];
         kh[a] = kh0[a];
       }
@@ -391,7 +396,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           hh[a] = h0[a] * sc;
-          kh[a] = kh0[a] / sc;
+          kh[a] = kh0[a] * pow2neg<R>(-lvl);   // exact: 1 / sc
         }
       }
       int64_t c = kOct ? leaf : cell_index(G, ci);
@@ -416,7 +421,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           }
         }
         if (tau.reached(ktot * tmin)) {
-          const R le = tau.value() / ktot;
+          const R le = m_div(tau.value(), ktot);
 #pragma unroll
           for (int a = 0; a < 3; ++a) xi[a].add(le * kh[a]);
           interact = true;
@@ -440,7 +445,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
               hh[a] = h0[a] * sc;
-              kh[a] = kh0[a] / sc;
+              kh[a] = kh0[a] * pow2neg<R>(-lvl);   // exact: 1 / sc
             }
           }
         } else {
@@ -463,7 +468,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         r0 = __ldg(rec + 2 * c);
         r1 = __ldg(rec + 2 * c + 1);
         const R ku_new = k[0] * R(r1.x) + k[1] * R(r1.y) + k[2] * R(r1.z);
-        x = (x + ku_old) * (R(r0.w) / ivth_old) - ku_new;
+        x = (x + ku_old) * m_div(R(r0.w), ivth_old) - ku_new;
       }
       lc[kCellVisits] += visits;
       COLT_MARK(4);
@@ -511,7 +516,15 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             atau0 = a * R(r0.x) * lmin + R(r1.w);
           }
           const R g = P.recoil ? R(kGoverA) * a : R(0);
-          ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3], b1, b2);
+          R xcw;
+          if (sxcw[0] == a) {
+            xcw = sxcw[1];
+          } else {
+            xcw = x_cw_fit<R>(a);
+            sxcw[0] = a;
+            sxcw[1] = xcw;
+          }
+          ScatterOut<R> so = scatter_hi<R>(x, k, a, g, atau0, P.phase, P.rng, rpid, event, b0.v[3], b1, b2, xcw);
           COLT_MARK(6);
           if (so.n_trials > kMaxTrials) {
             finish(3, 0.0);
@@ -723,7 +736,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 template <typename R, bool kOct>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
   constexpr int kWarps = 8;
-  const size_t smem = (sizeof(PeelEv<R>) + sizeof(int)) * 32 * kWarps;
+  const size_t smem = (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * kWarps;
   auto kern = k_transport<R, kWarps, kOct>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -751,7 +764,7 @@ static int grid_size_t(int blocks_per_sm, int sm_count) {
   constexpr int kWarps = 8;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<R, kWarps, kOct>, kWarps * 32,
-                                                (sizeof(PeelEv<R>) + sizeof(int)) * 32 * kWarps);
+                                                (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * kWarps);
   if (occ < 1) occ = 1;
   if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
   return occ * sm_count;
