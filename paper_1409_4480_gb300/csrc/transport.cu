@@ -226,6 +226,35 @@ k_transport(const LaunchDev* __restrict__ Lp) {
     e.kd = r0.z;
   };
 
+  // Next-event estimator cut (Sec. 6.1): a ray whose optical depth exceeds
+  // tau_esc_max adds nothing.  Every axis ray starts in the event's own cell;
+  // H(a, x) decreases with |x|, so (k_HI H(a, max_c |x_c|) + k_d) l_min bounds
+  // each ray's first-cell depth from below (x_c: the frequency the event sends
+  // towards camera c, over all six axis directions; l_min: the distance to the
+  // nearest face).  When the bound exceeds twice the cutoff (a margin far above
+  // H_approx's departures from monotonicity) no ray can contribute and the
+  // event is not peeled off; otherwise every ray is traced as usual.
+  auto peel_open = [&](int type, const R* kin, const R* ua, R upar, R g, R xin, const float4& rr0,
+                       const R hc[3]) -> bool {
+    const RunDev& P = J->p;
+    R xmax = fabs(xin);
+    if (type == 1) {
+      xmax = R(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const R base = xin - upar - g;
+        xmax = fmax(xmax, fabs(base + ua[q] + g * kin[q]));
+        xmax = fmax(xmax, fabs(base - ua[q] - g * kin[q]));
+      }
+    }
+    R lmin = R(3.0e38);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) lmin = fmin(lmin, fmin(xi[q].val(), xi[q].from_top()) * hc[q]);
+    lmin = fmax(lmin, R(0));
+    const R tau_lb = (R(rr0.x) * voigt<R>(R(rr0.y), xmax) + R(rr0.z)) * lmin;
+    return !(tau_lb > R(2) * prm<R>(P.tau_max, P.f.tau_max));
+  };
+
 #ifdef COLT_PHASE_CLOCKS
   // opt-in profiling build: SM cycles per phase of a round, printed per warp
   // (the lane maximum of each phase, exact for a warp with one live packet):
@@ -362,8 +391,14 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             finish(1, 0.0);     // source outside the box: leaves at line centre
           } else if (P.n_cam > 0) {
             const int64_t c = kOct ? leaf : cell_index(G, ci);
-            fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, __ldg(G.rec + 2 * c), __ldg(G.rec + 2 * c + 1));
-            has_peel = true;
+            const float4 e0 = __ldg(G.rec + 2 * c);
+            R hc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) hc[a] = prm<R>(G.h[a], G.hf[a]) * (kOct ? pow2neg<R>(lvl) : R(1));
+            if (peel_open(0, nullptr, nullptr, R(0), R(0), x, e0, hc)) {
+              fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, e0, __ldg(G.rec + 2 * c + 1));
+              has_peel = true;
+            }
           }
         } else {
           done = true;
@@ -495,7 +530,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             finish(2, 0.0);
             cont = false;
           } else {
-            if (P.n_cam > 0) {
+            if (P.n_cam > 0 && peel_open(0, nullptr, nullptr, R(0), R(0), x, r0, hh)) {
               fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, r0, r1);
               has_peel = true;
             }
@@ -532,7 +567,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           } else {
             ++nscat;
             ++nscat_hi;
-            if (P.n_cam > 0) {
+            if (P.n_cam > 0 && peel_open(1, k, so.u_atom, so.u_par, g, x, r0, hh)) {
               fill_event(1, k, so.u_atom, so.u_par, g, so.RQ, x, r0, r1);
               has_peel = true;
             }
