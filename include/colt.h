@@ -224,6 +224,11 @@ int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms);
 /* camera = -1: the angle-averaged escape spectrum (as doubles); else the
  * camera's peel-off spectrum.  nbins must match the request's bin count. */
 int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t nbins);
+/* The peel-off image cube of camera `camera` (0 <= camera < n_cam, npix > 0),
+ * laid out [v][u][bin] (npix x npix x cam_nbins doubles, Sec. 6.1 surface
+ * brightness per pixel and bin before unit conversion); n must equal that
+ * size (COLT_EINVAL otherwise). */
+int colt_read_image(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t n);
 int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out);
 int colt_release(colt_ctx* ctx, colt_req req);
 

@@ -27,7 +27,7 @@ COLT_PLAIN, COLT_MIXED = 0, 1
 
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
-           "colt_wait", "colt_read_spectrum", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
+           "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
            "colt_run_noalloc"]
 
 _LIB = None
@@ -120,6 +120,7 @@ def lib():
             "colt_poll": (I, [P, U64, C.POINTER(I), P]),
             "colt_wait": (I, [P, U64, D]),
             "colt_read_spectrum": (I, [P, U64, I, P, SZ]),
+            "colt_read_image": (I, [P, U64, I, P, SZ]),
             "colt_read_result": (I, [P, U64, P]),
             "colt_release": (I, [P, U64]),
             "colt_voigt": (I, [P, P, P, P, SZ, I, I]),
@@ -352,6 +353,13 @@ def colt_wait(ctx, req: int, timeout_ms: float = -1.0):
 def colt_read_spectrum(ctx, req: int, camera: int, nbins: int) -> np.ndarray:
     buf = np.zeros(nbins, np.float64)
     _check(ctx, lib().colt_read_spectrum(ctx, C.c_uint64(req), int(camera), _ptr(buf), nbins))
+    return buf
+
+
+def colt_read_image(ctx, req: int, camera: int, npix: int, nbins: int) -> np.ndarray:
+    """Image cube [v][u][bin] of one camera of a finished request."""
+    buf = np.zeros((npix, npix, nbins), np.float64)
+    _check(ctx, lib().colt_read_image(ctx, C.c_uint64(req), int(camera), _ptr(buf), buf.size))
     return buf
 
 

@@ -1130,6 +1130,24 @@ int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, siz
   return COLT_OK;
 }
 
+int colt_read_image(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t n) {
+  if (!ctx || !buf) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  Req& r = *it->second;
+  if (r.state != kDone) return fail(ctx, COLT_EAGAIN, "request not done");
+  if (camera < 0 || camera >= r.p.n_cam) return fail(ctx, COLT_EINVAL, "bad camera index");
+  const int np = r.p.cams[camera].npix;
+  if (np <= 0) return fail(ctx, COLT_EINVAL, "camera has no image");
+  if (n != (size_t)np * np * r.p.cam_nbins) return fail(ctx, COLT_EINVAL, "image size mismatch");
+  if (!r.tally.block || !r.tally.cam_image) { std::memset(buf, 0, sizeof(double) * n); return COLT_OK; }
+  CU(cudaMemcpyAsync(buf, r.tally.cam_image + r.run.cam[camera].img_off, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return COLT_OK;
+}
+
 int colt_release(colt_ctx* ctx, colt_req req) {
   if (!ctx) return COLT_EINVAL;
   std::lock_guard<std::recursive_mutex> lk(ctx->mu);

@@ -1,5 +1,5 @@
 """Serving through the C ABI: colt_submit / colt_poll / colt_wait /
-colt_read_spectrum with continuous batching.  Each request's result in the mix
+colt_read_spectrum / colt_read_image with continuous batching.  Each request's result in the mix
 equals its result alone (colt_run with the same grid and parameters):
 integer tallies bitwise, peel-off sums up to FP64 summation order.  Memory
 admission queues what does not fit and rejects what never can."""
@@ -18,6 +18,7 @@ def _mix():
              S.slab(16, 100.0, 1e5, v_max_kms=-50.0, tau_dust=0.2, nxy=4),
              S.sphere(16, 10.0, 3e4)]
     cams = S.axis_cameras(0)
+    cams[0] = S.Camera(cams[0].direction, 8)      # one camera with an 8 x 8 image
     reqs = []
     for i, (gi, n) in enumerate([(0, 3000), (1, 20000), (2, 1000), (0, 50000), (1, 700), (2, 9000)]):
         reqs.append((gi, S.RunSpec(n_packets=n, seed=4000 + i, albedo=0.32, spec_units=1, spec_lo=-400,
@@ -31,7 +32,7 @@ def test_batched_equals_alone(colt):
     try:
         grids, reqs = _mix()
         hs = [colt.colt_create_grid(ctx, g) for g in grids]
-        alone = [colt.colt_run(ctx, hs[gi], sp) for gi, sp in reqs]
+        alone = [colt.colt_run(ctx, hs[gi], sp, images=bool(sp.cameras)) for gi, sp in reqs]
         ids = []
         for gi, sp in reqs:                      # arrivals while earlier work runs
             ids.append(colt.colt_submit(ctx, hs[gi], sp))
@@ -49,6 +50,11 @@ def test_batched_equals_alone(colt):
                 assert np.allclose(got["cam_spec"], ref["cam_spec"], rtol=1e-9, atol=1e-300)
                 c0 = colt.colt_read_spectrum(ctx, rid, 0, sp.cam_nbins)
                 assert np.allclose(c0, ref["cam_spec"][0], rtol=1e-9, atol=1e-300)
+                img = colt.colt_read_image(ctx, rid, 0, 8, sp.cam_nbins)
+                assert np.allclose(img.ravel(), ref["cam_image"][: img.size], rtol=1e-9, atol=1e-300)
+                assert img.sum() > 0
+                with pytest.raises(colt.ColtError):
+                    colt.colt_read_image(ctx, rid, 1, 8, sp.cam_nbins)     # camera 1 has no image
             esc = colt.colt_read_spectrum(ctx, rid, -1, sp.spec_nbins)
             assert np.array_equal(esc, ref["spec"].astype(np.float64))
             colt.colt_release(ctx, rid)
