@@ -331,8 +331,10 @@ def colt_solve(ctx, grid, spec, f_nl: float = 0.5, images: bool = False) -> dict
 
 
 # ------------------------------------------------------------------ serving --
-def colt_submit(ctx, grid: int, spec) -> int:
-    p, cams = run_params(spec, False)
+def colt_submit(ctx, grid: int, spec, images: bool = True) -> int:
+    """Queue a solve.  Cameras with npix > 0 tally image cubes unless
+    images=False (then only their spectra are tallied)."""
+    p, cams = run_params(spec, images)
     h = C.c_uint64()
     _check(ctx, lib().colt_submit(ctx, C.c_uint64(grid), C.byref(p), C.byref(h)))
     return h.value
