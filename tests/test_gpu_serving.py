@@ -34,6 +34,7 @@ def test_batched_equals_alone(colt):
         hs = [colt.colt_create_grid(ctx, g) for g in grids]
         alone = [colt.colt_run(ctx, hs[gi], sp, images=bool(sp.cameras)) for gi, sp in reqs]
         ids = []
+        image_flux = 0.0
         for gi, sp in reqs:                      # arrivals while earlier work runs
             ids.append(colt.colt_submit(ctx, hs[gi], sp))
             colt.colt_poll(ctx, ids[-1])
@@ -52,12 +53,16 @@ def test_batched_equals_alone(colt):
                 assert np.allclose(c0, ref["cam_spec"][0], rtol=1e-9, atol=1e-300)
                 img = colt.colt_read_image(ctx, rid, 0, 8, sp.cam_nbins)
                 assert np.allclose(img.ravel(), ref["cam_image"][: img.size], rtol=1e-9, atol=1e-300)
-                assert img.sum() > 0
+                # the image plane spans the box: every +x contribution lands in it
+                # (none on the periodic slab, whose x axis has no observer)
+                assert img.sum() == pytest.approx(ref["cam_spec"][0].sum(), rel=1e-9, abs=1e-300)
+                image_flux += img.sum()
                 with pytest.raises(colt.ColtError):
                     colt.colt_read_image(ctx, rid, 1, 8, sp.cam_nbins)     # camera 1 has no image
             esc = colt.colt_read_spectrum(ctx, rid, -1, sp.spec_nbins)
             assert np.array_equal(esc, ref["spec"].astype(np.float64))
             colt.colt_release(ctx, rid)
+        assert image_flux > 0
         for h in hs:
             colt.colt_destroy_grid(ctx, h)
     finally:
