@@ -320,3 +320,23 @@ def test_full_size_sampled_packets(O, colt, ctx):
             got = {k: rg[k][sl] for k in ("pk_status", "pk_nscat", "pk_freq")}
             full, same = _identity(got, ro, crit[i][0])
             assert full >= crit[i][1], (i, pid0, same, full)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_serving_mix_parameter_corners(O, colt, ctx, precision):
+    # corners of the serving mix's parameter ranges (sphere or slab, T from 10 K
+    # to 1e5 K, tau0 1e4 to 1e8, v_max +-300 km/s, dust tau 0 to 2) on small grids
+    corners = [("sphere", 10.0, 1e8, 0.0, 0.0), ("slab", 1e5, 1e4, 300.0, 2.0), ("sphere", 1e5, 1e6, -300.0, 1.0),
+               ("slab", 10.0, 1e6, -150.0, 0.5)]
+    for geom, T, tau0, v, td in corners:
+        g = S.sphere(16, T, tau0, v_max_kms=v, tau_dust=td) if geom == "sphere" else \
+            S.slab(16, T, tau0, v_max_kms=v, tau_dust=td, nxy=4)
+        vth = 12.85 * np.sqrt(T / 1e4)
+        w = 40.0 * vth + abs(v)
+        spec = S.RunSpec(n_packets=1500, seed=4100, albedo=0.32, spec_units=1, spec_lo=-w, spec_hi=w, spec_nbins=100,
+                         max_scatter=PREFIX)
+        rg, ro = _run_both(O, colt, ctx, g, spec, precision)
+        _conserved(rg, 1500)
+        full, same = _identity(rg, ro, FTOL[precision])
+        print(f"{geom} T={T:g} tau0={tau0:g}: identical {same:.4f}, with frequency {full:.4f}")
+        assert full >= MIN_SAME[precision]
