@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double),
                 ("cam_nbins", C.c_int), ("fov_half", C.c_double), ("n_threads", C.c_int),
                 ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p),
-                ("pid0", C.c_uint64)]
+                ("pid0", C.c_uint64), ("emission", C.c_int)]
 
 
 class Result(C.Structure):
@@ -244,6 +244,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     p.tau_esc_max = float(spec.tau_esc_max)
     p.albedo = float(spec.albedo)
     p.max_scatter = int(spec.max_scatter)
+    p.emission = int(getattr(spec, "emission", 0) or 0)
     p.spec_units = int(spec.spec_units)
     p.T_ref = float(spec.T_ref)
     p.spec_lo, p.spec_hi, p.spec_nbins = float(spec.spec_lo), float(spec.spec_hi), int(spec.spec_nbins)

@@ -134,6 +134,7 @@ typedef struct {
   double*   pk_freq;        /* escape spectral coordinate; for packets capped by
                                max_scatter the lab frequency at the cap        */
   uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
+  int       emission;       /* 0 line centre (x = 0), 1 natural + thermal        */
 } o_params;
 
 typedef struct {

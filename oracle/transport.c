@@ -209,6 +209,19 @@ static void run_packet(worker* w, uint64_t idx) {
     /* source outside the domain: leaves at once, at line centre */
     status = 1;
     s_esc = 0.0;
+  } else if (p->emission == 1) {
+    /* Sec. 3.1.1: x_i = x_nat + k_i.u_atom in the source cell's frame, x_nat
+     * from the natural (Lorentzian) profile a / (pi (x^2 + a^2)) and each atom
+     * velocity component (in units of v_th) Gaussian of variance 1/2.  Draws:
+     * block 0 word 3 (x_nat), block 2 (Box-Muller: u_x, u_y from words 0-1,
+     * u_z from words 2-3).  The emission is isotropic in the atom's frame, so
+     * the photon sent towards a camera has x_nat + k_c.u_atom (W = 1). */
+    double B2[4];
+    draw_block(w->key, pid, 0, 2, B2);
+    double rho1 = sqrt(-log(B2[0])), rho2 = sqrt(-log(B2[2]));
+    double ua[3] = {rho1 * cos(2.0 * O_PI * B2[1]), rho1 * sin(2.0 * O_PI * B2[1]), rho2 * cos(2.0 * O_PI * B2[3])};
+    x = g->a[c] * tan(O_PI * (B0[3] - 0.5)) + dot3(k, ua);
+    peel_all_hi(w, r, c, x, k, ua, 0.0, 0.0);
   } else {
     peel_all_iso(w, r, c, x);
   }

@@ -96,6 +96,7 @@ class RunSpec:
     fov_half: float = 0.0           # 0 -> half of the box width
     precision: int = 1              # 0 plain FP64, 1 mixed (FP32 transport)
     pid_offset: int = 0             # packets are ids pid_offset .. pid_offset + n_packets - 1
+    emission: int = 0               # 0 line centre, 1 natural (Lorentzian) + thermal atom velocity
 
 
 def sigma0_recipe(T: float) -> float:

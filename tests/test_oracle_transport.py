@@ -234,3 +234,34 @@ def test_face_transform_preserves_lab_frequency(O):
     cs = r["cam_spec"]
     for cam, b in zip(range(6), [5, 5, 5, 5, 0, 9]):
         assert cs[cam, b] == pytest.approx(N, rel=1e-9)
+
+
+def test_natural_thermal_emission_is_the_voigt_profile(O):
+    # Sec. 3.1.1: x = x_nat + k.u_atom with a Lorentzian x_nat of width a and a
+    # Maxwellian atom velocity; in an empty box every packet leaves unscattered
+    # with that frequency, whose distribution is the Voigt profile H(a,x)/sqrt(pi)
+    # (a convolution of the two).  Pinned against the exact H from the Faddeeva
+    # function, independently of the oracle's H_approx.  The emission peel-off
+    # towards each camera samples the same profile.
+    T, N = 10.0, 60000
+    g = S.uniform_box((4, 4, 4), (-1e18,) * 3, (1e18,) * 3, 1e-30, T)
+    edges = np.linspace(-6.0, 6.0, 49)
+    spec = S.RunSpec(n_packets=N, seed=61, emission=1, T_ref=T, spec_units=0, spec_lo=-6.0, spec_hi=6.0,
+                     spec_nbins=48, cameras=S.axis_cameras(0, ("+x", "-z")), cam_units=0, cam_lo=-6.0, cam_hi=6.0,
+                     cam_nbins=48)
+    r = O.run(g, spec)
+    assert r["n_escaped"] == N and r["n_scat"] == 0
+    a = O.damping_a(T)
+    xs = np.linspace(-6.0, 6.0, 48 * 64 + 1)
+    prof = np.real(wofz(xs + 1j * a)) / np.sqrt(np.pi)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (prof[1:] + prof[:-1]) * np.diff(xs))])
+    p_bins = np.diff(np.interp(edges, xs, cdf))
+    tail = 1.0 - cdf[-1]                       # |x| > 6: the Lorentzian wings
+    counts = r["spec"].astype(float)
+    assert abs(r["spec_under"] + r["spec_over"] - N * tail) <= 4 * np.sqrt(N * tail) + 2
+    chi2 = np.sum((counts - N * p_bins) ** 2 / (N * p_bins))
+    assert stats.chi2.sf(chi2, len(p_bins) - 1) > 1e-3
+    for cam in range(2):
+        w = r["cam_spec"][cam]
+        assert np.sum(w) == pytest.approx(N * cdf[-1], rel=0.02)
+        assert np.sum(np.abs(w / np.sum(w) - p_bins / p_bins.sum())) < 0.05
