@@ -52,6 +52,7 @@ enum { COLT_MEM_HOST = 0, COLT_MEM_DEVICE = 1 };
 enum { COLT_PLAIN = 0, COLT_MIXED = 1 };          /* arithmetic of the transport */
 enum { COLT_PHASE_DIPOLE = 0, COLT_PHASE_ISOTROPIC = 1 };
 enum { COLT_UNITS_X = 0, COLT_UNITS_DV_KMS = 1 };
+enum { COLT_EMIT_LINE_CENTRE = 0, COLT_EMIT_NATURAL_THERMAL = 1 };   /* Sec. 3.1.1 */
 
 /* ------------------------------------------------------------- context -- */
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds what the
@@ -147,6 +148,10 @@ typedef struct {
                                (random streams are keyed by id, so a job split into
                                id ranges -- batches, replicas -- sums to the same
                                tallies); per-packet outputs are indexed from 0      */
+  int emission;             /* COLT_EMIT_LINE_CENTRE: x = 0 in the source cell's frame;
+                               COLT_EMIT_NATURAL_THERMAL: x = x_nat + k.u_atom with a
+                               Lorentzian x_nat (width a) and a Maxwellian atom velocity
+                               of the source cell (Sec. 3.1.1)                      */
 } colt_run_params;
 
 /* Outputs of a run.  Counters are always filled; every array pointer may be

@@ -59,7 +59,7 @@ class RunParams(C.Structure):
                 ("spec_hi", C.c_double), ("spec_nbins", C.c_int), ("n_cam", C.c_int), ("cams", C.c_void_p),
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double), ("cam_nbins", C.c_int),
                 ("fov_half", C.c_double), ("precision", C.c_int), ("block_size", C.c_int),
-                ("blocks_per_sm", C.c_int), ("pid_offset", C.c_uint64)]
+                ("blocks_per_sm", C.c_int), ("pid_offset", C.c_uint64), ("emission", C.c_int)]
 
 
 class Result(C.Structure):
@@ -259,6 +259,7 @@ def run_params(spec, images: bool = False):
     p.block_size = 0
     p.blocks_per_sm = int(getattr(spec, "blocks_per_sm", 0) or 0)
     p.pid_offset = int(getattr(spec, "pid_offset", 0) or 0)
+    p.emission = int(getattr(spec, "emission", 0) or 0)
     return p, cams
 
 

@@ -191,6 +191,8 @@ int validate_params(colt_ctx* ctx, const colt_run_params* p) {
   }
   if (p->precision != COLT_PLAIN && p->precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
   if (p->phase != COLT_PHASE_DIPOLE && p->phase != COLT_PHASE_ISOTROPIC) return fail(ctx, COLT_EINVAL, "bad phase");
+  if (p->emission != COLT_EMIT_LINE_CENTRE && p->emission != COLT_EMIT_NATURAL_THERMAL)
+    return fail(ctx, COLT_EINVAL, "bad emission mode");
   if (p->spec_units != COLT_UNITS_X && p->spec_units != COLT_UNITS_DV_KMS) return fail(ctx, COLT_EINVAL, "bad spec_units");
   if (p->n_cam > 0 && p->cam_units != COLT_UNITS_X && p->cam_units != COLT_UNITS_DV_KMS)
     return fail(ctx, COLT_EINVAL, "bad cam_units");
@@ -263,6 +265,7 @@ RunDev make_run(const GridObj& g, const colt_run_params* p) {
   r.core_skip = p->core_skip ? 1 : 0;
   r.recoil = p->recoil ? 1 : 0;
   r.phase = p->phase;
+  r.emission = p->emission;
   r.tau_max = p->tau_esc_max;
   r.albedo = p->albedo;
   r.max_scatter = p->max_scatter;

@@ -82,6 +82,7 @@ struct RunDev {
   double src[3] = {0, 0, 0};
   double src_sigma = 0;
   int core_skip = 1, recoil = 1, phase = 0;
+  int emission = 0;           // 0 line centre, 1 natural + thermal (Sec. 3.1.1)
   double tau_max = 50.0;
   double albedo = 0.0;
   uint64_t max_scatter = ~0ull;

@@ -94,6 +94,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     const colt_device_tallies& t = tallies[i];
     if (!gv.records || gv.nx <= 0 || gv.ny <= 0 || gv.nz <= 0) return COLT_EINVAL;
     if (p.precision != precision || (p.precision != COLT_PLAIN && p.precision != COLT_MIXED)) return COLT_EINVAL;
+    if (p.emission != COLT_EMIT_LINE_CENTRE && p.emission != COLT_EMIT_NATURAL_THERMAL) return COLT_EINVAL;
     if (p.spec_nbins <= 0 || !(p.spec_hi > p.spec_lo) || !t.spec || !t.counters) return COLT_EINVAL;
     if (p.n_cam < 0 || p.n_cam > kMaxCams) return COLT_EINVAL;
     if (p.n_cam > 0 && (!p.cams || p.cam_nbins <= 0 || !(p.cam_hi > p.cam_lo) || !t.cam_spec || !t.cam_spec2))
@@ -126,6 +127,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     r.core_skip = p.core_skip ? 1 : 0;
     r.recoil = p.recoil ? 1 : 0;
     r.phase = p.phase;
+    r.emission = p.emission;
     r.tau_max = p.tau_esc_max;
     r.albedo = p.albedo;
     r.max_scatter = p.max_scatter;

@@ -389,15 +389,36 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           alive = true;
           if (!inside) {
             finish(1, 0.0);     // source outside the box: leaves at line centre
-          } else if (P.n_cam > 0) {
+          } else {
             const int64_t c = kOct ? leaf : cell_index(G, ci);
             const float4 e0 = __ldg(G.rec + 2 * c);
-            R hc[3];
+            R ua[3] = {R(0), R(0), R(0)};
+            R upar = R(0);
+            if (P.emission == 1) {
+              // Sec. 3.1.1: x = x_nat + k.u_atom, x_nat Lorentzian of width a (block
+              // 0 word 3), u_atom Maxwellian, variance 1/2 per component (block 2,
+              // Box-Muller pairs); the peel-off sends x_nat + k_c.u_atom, W = 1
+              const U4<R> b2 = uniforms<R>(P.rng, rpid, 0, 2);
+              R s1, c1, s2, c2, sl, cl;
+              m_sincospi(R(2) * b2.v[1], &s1, &c1);
+              m_sincospi(R(2) * b2.v[3], &s2, &c2);
+              m_sincospi(b0.v[3] - R(0.5), &sl, &cl);
+              const R rho1 = m_sqrt(-m_log(b2.v[0])), rho2 = m_sqrt(-m_log(b2.v[2]));
+              ua[0] = rho1 * c1;
+              ua[1] = rho1 * s1;
+              ua[2] = rho2 * c2;
+              upar = k[0] * ua[0] + k[1] * ua[1] + k[2] * ua[2];
+              x = R(e0.y) * m_div(sl, cl) + upar;
+            }
+            if (P.n_cam > 0) {
+              R hc[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) hc[a] = prm<R>(G.h[a], G.hf[a]) * (kOct ? pow2neg<R>(lvl) : R(1));
-            if (peel_open(0, nullptr, nullptr, R(0), R(0), x, e0, hc)) {
-              fill_event(0, nullptr, nullptr, R(0), R(0), R(0), x, e0, __ldg(G.rec + 2 * c + 1));
-              has_peel = true;
+              for (int a = 0; a < 3; ++a) hc[a] = prm<R>(G.h[a], G.hf[a]) * (kOct ? pow2neg<R>(lvl) : R(1));
+              const int ty = P.emission == 1 ? 1 : 0;
+              if (peel_open(ty, k, ua, upar, R(0), x, e0, hc)) {
+                fill_event(ty, ty ? k : nullptr, ty ? ua : nullptr, upar, R(0), R(0), x, e0, __ldg(G.rec + 2 * c + 1));
+                has_peel = true;
+              }
             }
           }
         } else {

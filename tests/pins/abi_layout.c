@@ -11,6 +11,7 @@ int main(void) {
   printf("colt_scatter_io %zu\n", sizeof(colt_scatter_io));
   printf("off_scatter_n_trials %zu\n", offsetof(colt_scatter_io, n_trials));
   printf("off_run_precision %zu\n", offsetof(colt_run_params, precision));
+  printf("off_run_emission %zu\n", offsetof(colt_run_params, emission));
   printf("off_result_pk_freq %zu\n", offsetof(colt_result, pk_freq));
   return 0;
 }

@@ -57,6 +57,7 @@ def test_binding_struct_layout_matches_header():
     assert sizes["colt_scatter_io"] == ctypes.sizeof(colt.ScatterIO)
     assert sizes["off_scatter_n_trials"] == colt.ScatterIO.n_trials.offset
     assert sizes["off_run_precision"] == colt.RunParams.precision.offset
+    assert sizes["off_run_emission"] == colt.RunParams.emission.offset
     assert sizes["off_result_pk_freq"] == colt.Result.pk_freq.offset
 
 

@@ -340,3 +340,26 @@ def test_serving_mix_parameter_corners(O, colt, ctx, precision):
         full, same = _identity(rg, ro, FTOL[precision])
         print(f"{geom} T={T:g} tau0={tau0:g}: identical {same:.4f}, with frequency {full:.4f}")
         assert full >= MIN_SAME[precision]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_natural_thermal_emission(O, colt, ctx, precision):
+    # Sec. 3.1.1 emission x = x_nat + k.u_atom: in an empty box every packet
+    # leaves with its emitted frequency (per packet equal to the oracle's, and the
+    # emission peel-off towards each camera uses x_nat + k_c.u_atom); in the
+    # dusty outflow the 20-scattering prefixes agree as with line-centre emission
+    T, N = 10.0, 4000
+    g = S.uniform_box((4, 4, 4), (-1e18,) * 3, (1e18,) * 3, 1e-30, T)
+    spec = S.RunSpec(n_packets=N, seed=62, emission=1, T_ref=T, spec_units=0, spec_lo=-6.0, spec_hi=6.0,
+                     spec_nbins=48, cameras=S.axis_cameras(0), cam_units=0, cam_lo=-6.0, cam_hi=6.0, cam_nbins=48)
+    rg, ro = _run_both(O, colt, ctx, g, spec, precision)
+    assert rg["n_escaped"] == N and rg["n_scat"] == 0
+    ftol = 1e-12 if precision == 0 else 1e-5
+    assert np.all(np.abs(rg["pk_freq"] - ro["pk_freq"]) <= ftol * np.maximum(1.0, np.abs(ro["pk_freq"])))
+    assert np.allclose(rg["cam_spec"], ro["cam_spec"], rtol=1e-9 if precision == 0 else 1e-3, atol=1e-9)
+    g, spec = dusty_outflow()
+    spec.n_packets, spec.max_scatter, spec.emission = 3000, PREFIX, 1
+    rg, ro = _run_both(O, colt, ctx, g, spec, precision, images=True)
+    full, same = _identity(rg, ro, FTOL[precision])
+    print(f"precision {precision}: identical {same:.4f}, with frequency {full:.4f}")
+    assert full >= MIN_SAME[precision]
