@@ -217,16 +217,18 @@ def small_cosmo():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_cosmo_box_prefix_identity(O, colt, ctx, precision):
-    # sources at the highest peaks of the FFT grid lie on octree split planes
-    # (both sides apply the same tie rule); the oracle against itself with an
-    # off-plane source moved by a relative 1e-9 keeps 99.3% of the
-    # 20-scattering frequencies within 1e-3 (1e-7: 91%), as in the halo
+    # Sources at the highest peaks of the FFT grid lie on octree split planes
+    # (both sides apply the same tie rule).  This medium is the most chaotic:
+    # the oracle against itself with every input field moved by one FP32 ulp
+    # (the resolution of the GPU's cell records) keeps 88.8-90% of the
+    # 20-scattering frequencies within 1e-3, but 99.4-99.6% of 10-scattering
+    # ones, so the prefix here is 10 scatterings.
     g, src = small_cosmo()
     assert len(np.unique(g.leaf_level)) >= 3
     for j in (0, 3):
         spec = S.RunSpec(n_packets=2000, seed=51 + j, albedo=0.32, spec_units=1, spec_lo=-500, spec_hi=500,
                          spec_nbins=100, cameras=S.axis_cameras(0, ("+x", "+y", "+z")), cam_lo=-500, cam_hi=500,
-                         cam_nbins=50, src_pos=src[j], max_scatter=PREFIX, precision=precision)
+                         cam_nbins=50, src_pos=src[j], max_scatter=10, precision=precision)
         rg = _run(colt, ctx, g, spec)
         ro = O.run(g, spec, per_packet=True)
         full, disc = _identity(rg, ro)

@@ -354,13 +354,12 @@ def test_natural_thermal_emission(O, colt, ctx, precision):
                      spec_nbins=48, cameras=S.axis_cameras(0), cam_units=0, cam_lo=-6.0, cam_hi=6.0, cam_nbins=48)
     rg, ro = _run_both(O, colt, ctx, g, spec, precision)
     assert rg["n_escaped"] == N and rg["n_scat"] == 0
-    ftol = 1e-12 if precision == 0 else 1e-5
+    # both paths read the FP32 cell records (a, 1/v_th): ~1e-7 relative
+    ftol = 1e-6 if precision == 0 else 1e-5
     assert np.all(np.abs(rg["pk_freq"] - ro["pk_freq"]) <= ftol * np.maximum(1.0, np.abs(ro["pk_freq"])))
-    if precision == 0:
-        assert np.allclose(rg["cam_spec"], ro["cam_spec"], rtol=1e-9, atol=1e-9)
-    else:   # a frequency within FP32 rounding of a bin edge may change bins
-        assert np.allclose(rg["cam_spec"].sum(axis=1), ro["cam_spec"].sum(axis=1), rtol=1e-6)
-        assert np.sum(np.abs(rg["cam_spec"] - ro["cam_spec"])) <= 0.01 * np.sum(ro["cam_spec"])
+    # a frequency within rounding of a bin edge may change bins
+    assert np.allclose(rg["cam_spec"].sum(axis=1), ro["cam_spec"].sum(axis=1), rtol=1e-6)
+    assert np.sum(np.abs(rg["cam_spec"] - ro["cam_spec"])) <= 0.01 * np.sum(ro["cam_spec"])
     g, spec = dusty_outflow()
     spec.n_packets, spec.max_scatter, spec.emission = 3000, PREFIX, 1
     rg, ro = _run_both(O, colt, ctx, g, spec, precision, images=True)
