@@ -246,6 +246,8 @@ def run_gpu(args):
     img = not args.no_images
     grids_h = [case_grid(t, v) for t, v in cases()]
     hs = [C.colt_create_grid(ctx, g) for g in grids_h]
+    # launch configuration measured on the static tau0 = 1e6 case (before warm-up)
+    tuned = C.colt_autotune(ctx, hs[4], case_spec(4, B, 0, images=False))
 
     def specs_of(s):
         off = (s * world + rank) * B          # disjoint packet ids per (step, rank)
@@ -366,6 +368,8 @@ def run_gpu(args):
                        "cameras": "6 x 128^2 x 200" if img else "6 x 200 (no images)",
                        "grid": "128^3 Cartesian, 32 B records", "precision": "mixed (FP32 transport, FP64 tau/escape)",
                        "launch": "served: colt_submit of 9 solves per step, persistent launches in flight",
+                       "launch_config": {"variant": tuned["variant"], "blocks_per_sm": tuned["blocks_per_sm"],
+                                         "source": "colt_autotune on the tau0=1e6 static case"},
                        "l2": "records 9 x 67 MB + tallies 9 x 157 MB per step > 129 MB L2: inputs larger than L2"},
             "gpu_launches": launches,
             "counts": {"scatterings": tot_scat, "packets": tot_pk,

@@ -193,6 +193,24 @@ int colt_run(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_resul
 int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
                    colt_result* out);
 
+/* ------------------------------------------------------------ autotune -- */
+/* Launch configuration of the persistent transport kernel: a register
+ * variant (0: the compiler's allocation; 1: registers capped so that four
+ * 256-thread CTAs fit on an SM, FP32 only) and the resident CTAs per SM
+ * (0 = as many as fit).  The library default is {0, 0}. */
+typedef struct {
+  int variant;
+  int blocks_per_sm;
+  double scatterings_per_s;  /* measured by colt_autotune */
+} colt_launch_config;
+
+/* Measure short solves of (grid, *params) -- two waves of packets, histories
+ * capped at 256 scatterings, no images -- under every configuration the
+ * build offers, keep the fastest for params->precision and the grid's kind
+ * (every later launch of that pair with blocks_per_sm = 0 uses it, served
+ * launches included) and report it in *out (may be NULL).  Blocking. */
+int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out);
+
 /* Same solve with HOST input fields: builds a temporary grid from desc, runs,
  * copies results back and frees the grid (one call for an end-to-end user). */
 int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params* p, colt_result* out);

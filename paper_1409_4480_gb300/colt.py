@@ -28,7 +28,7 @@ COLT_PLAIN, COLT_MIXED = 0, 1
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
            "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
-           "colt_run_noalloc"]
+           "colt_run_noalloc", "colt_autotune"]
 
 _LIB = None
 
@@ -76,6 +76,10 @@ class Stats(C.Structure):
     _fields_ = [("done", C.c_int), ("admitted", C.c_int), ("packets_done", C.c_uint64),
                 ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double),
                 ("ctx_launches", C.c_uint64)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("variant", C.c_int), ("blocks_per_sm", C.c_int), ("scatterings_per_s", C.c_double)]
 
 
 class ScatterIO(C.Structure):
@@ -126,6 +130,7 @@ def lib():
             "colt_voigt": (I, [P, P, P, P, SZ, I, I]),
             "colt_scatter": (I, [P, P, SZ, U64, I]),
             "colt_run_noalloc": (I, [I, P, P, P, P]),
+            "colt_autotune": (I, [P, U64, P, P]),
         }
         for name, (rt, args) in sig.items():
             f = getattr(L, name)
@@ -332,6 +337,15 @@ def colt_solve(ctx, grid, spec, f_nl: float = 0.5, images: bool = False) -> dict
 
 
 # ------------------------------------------------------------------ serving --
+def colt_autotune(ctx, grid: int, spec) -> dict:
+    """Measure and keep the fastest launch configuration for the spec's
+    precision and the grid's kind (see colt.h)."""
+    p, cams = run_params(spec, False)
+    out = LaunchConfig()
+    _check(ctx, lib().colt_autotune(ctx, C.c_uint64(grid), C.byref(p), C.byref(out)))
+    return dict(variant=out.variant, blocks_per_sm=out.blocks_per_sm, scatterings_per_s=out.scatterings_per_s)
+
+
 def colt_submit(ctx, grid: int, spec, images: bool = True) -> int:
     """Queue a solve.  Cameras with npix > 0 tally image cubes unless
     images=False (then only their spectra are tallied)."""

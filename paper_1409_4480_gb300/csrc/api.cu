@@ -83,6 +83,7 @@ struct Slot {
   bool in_flight = false;
   std::vector<std::pair<uint64_t, uint64_t>> jobs;  // (request id, packets)
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][grid kind]
+  int graph_cfg[2][2] = {{-1, -1}, {-1, -1}};                               // launch configuration captured
 };
 
 struct Tally {
@@ -141,6 +142,8 @@ struct colt_ctx {
   std::mutex cv_mu;
   std::condition_variable cv;
   uint64_t done_seq = 0;
+  // launch configuration per [precision][grid kind] (colt_autotune)
+  colt_launch_config cfg[2][2] = {{{0, 0, 0.0}, {0, 0, 0.0}}, {{0, 0, 0.0}, {0, 0, 0.0}}};
 };
 
 namespace {
@@ -346,23 +349,29 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
   LaunchBuf& lb = sl.lb;
   const int gi = precision == COLT_PLAIN ? 0 : 1;
   const int gk = kind == COLT_OCTREE ? 1 : 0;
+  const colt_launch_config& cfg = ctx->cfg[gi][gk];
   ++ctx->launches;
   if (blocks_per_sm > 0) {
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
     CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
-    CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, blocks_per_sm, ctx->sm_count,
-                        sl.stream));
+    CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant, blocks_per_sm,
+                        ctx->sm_count, sl.stream));
     CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
+  }
+  const int code = cfg.variant * 64 + cfg.blocks_per_sm;
+  if (sl.graph[gi][gk] && sl.graph_cfg[gi][gk] != code) {
+    cudaGraphExecDestroy(sl.graph[gi][gk]);
+    sl.graph[gi][gk] = nullptr;
   }
   if (!sl.graph[gi][gk]) {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
     cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
-    cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, 0, ctx->sm_count,
-                                      sl.stream);
+    cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant,
+                                      cfg.blocks_per_sm, ctx->sm_count, sl.stream);
     cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                     cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
@@ -371,6 +380,7 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     cudaError_t ie = cudaGraphInstantiate(&sl.graph[gi][gk], g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    sl.graph_cfg[gi][gk] = code;
   }
   CU(cudaGraphLaunch(sl.graph[gi][gk], sl.stream));
   return COLT_OK;
@@ -986,6 +996,57 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
 int colt_run(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_result* out) {
   if (!ctx || !out || !p) return COLT_EINVAL;
   return colt_run_batch(ctx, 1, &grid, p, out);
+}
+
+int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out) {
+  if (!ctx || !params) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  auto it = ctx->grids.find(grid);
+  if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+  int rc = validate_params(ctx, params);
+  if (rc) return rc;
+  const int prec = params->precision;
+  const int kind = it->second.dev.kind;
+  const int gi = prec == COLT_PLAIN ? 0 : 1, gk = kind == COLT_OCTREE ? 1 : 0;
+  // calibration solve: the request's own grid and parameters, two waves of
+  // packets over the largest launch, histories capped at 256 scatterings (the
+  // steady state the configuration decides), no images
+  colt_run_params q = *params;
+  std::vector<colt_camera> cams(params->cams, params->cams + params->n_cam);
+  for (auto& c : cams) c.npix = 0;
+  q.cams = cams.data();
+  q.blocks_per_sm = 0;
+  q.max_scatter = (q.max_scatter == 0 || q.max_scatter > 256) ? 256 : q.max_scatter;
+  q.n_packets = (uint64_t)ctx->sm_count * 4 * 256 * 2;
+  std::vector<uint64_t> spec(q.spec_nbins);
+  std::vector<double> cs((size_t)std::max(1, q.n_cam) * q.cam_nbins), cs2(cs.size());
+  colt_launch_config best{0, 0, -1.0};
+  for (int v = 0; v < transport_variants(prec); ++v) {
+    const int occ = transport_occupancy(prec, kind, v);
+    for (int b = occ; b >= std::max(1, occ - 1); --b) {
+      ctx->cfg[gi][gk] = colt_launch_config{v, b, 0.0};
+      double rate = 0.0;
+      for (int rep = 0; rep < 2; ++rep) {          // the first run warms the configuration up
+        colt_result r{};
+        r.spec = spec.data();
+        if (q.n_cam > 0) {
+          r.cam_spec = cs.data();
+          r.cam_spec2 = cs2.data();
+        }
+        rc = colt_run_batch(ctx, 1, &grid, &q, &r);
+        if (rc) {
+          ctx->cfg[gi][gk] = colt_launch_config{0, 0, 0.0};
+          return rc;
+        }
+        rate = r.kernel_ms > 0 ? (double)r.n_scat / (r.kernel_ms * 1e-3) : 0.0;
+      }
+      if (rate > best.scatterings_per_s) best = colt_launch_config{v, b, rate};
+    }
+  }
+  ctx->cfg[gi][gk] = best;
+  if (out) *out = best;
+  return COLT_OK;
 }
 
 int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params* p, colt_result* out) {

@@ -151,10 +151,14 @@ struct LaunchDev {
 // launchers (transport.cu)
 // L is a DEVICE pointer to the launch header (so a captured graph can replay it).
 // All jobs of a launch share one grid kind (COLT_CARTESIAN / COLT_OCTREE).
-cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int blocks_per_sm, int sm_count,
-                             cudaStream_t s);
-// persistent grid size the launcher uses for a precision and grid kind
-int transport_grid_size(int precision, int kind, int blocks_per_sm, int sm_count);
+// variant: 0 = the compiler's register allocation, 1 = registers capped for
+// four CTAs per SM (FP32 only; transport_variants gives the count);
+// blocks_per_sm 0 = as many CTAs as fit.
+cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
+                             int sm_count, cudaStream_t s);
+int transport_variants(int precision);
+// resident CTAs per SM of a variant
+int transport_occupancy(int precision, int kind, int variant);
 // grid preparation (grid.cu)
 cudaError_t launch_atau_nl(const GridDev& g, const float* n_hi, double f_nl, float4* rec_mut, cudaStream_t s);
 // octree grids: lev / ijk are the device copies of the leaves' levels and coordinates

@@ -195,7 +195,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     return COLT_ECUDA;
   if (cudaMemcpyAsync(scratch, host, kOffJobs + sizeof(Job) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return COLT_ECUDA;
-  if (total > 0 && launch_transport(reinterpret_cast<const LaunchDev*>(scratch), precision, COLT_CARTESIAN,
+  if (total > 0 && launch_transport(reinterpret_cast<const LaunchDev*>(scratch), precision, COLT_CARTESIAN, 0,
                                     params[0].blocks_per_sm, sm_count, stream) != cudaSuccess)
     return COLT_ECUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return COLT_ECUDA;

@@ -116,8 +116,10 @@ __device__ __forceinline__ int64_t cell_index(const GridDev& G, const int c3[3])
   return (int64_t)c3[0] + G.stride[1] * c3[1] + G.stride[2] * c3[2];
 }
 
-template <typename R, int kWarps, bool kOct>
-__global__ void __launch_bounds__(kWarps * 32)
+// kMinBlocks: resident CTAs per SM the register allocation must allow (1: the
+// compiler's choice, 80 registers and 3 CTAs/SM for FP32; 4: 64 registers)
+template <typename R, int kWarps, bool kOct, int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_transport(const LaunchDev* __restrict__ Lp) {
   const LaunchDev L = *Lp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -789,11 +791,16 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #undef COLT_MARK
 }
 
-template <typename R, bool kOct>
+template <typename R>
+constexpr size_t transport_smem() {
+  return (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * 8;
+}
+
+template <typename R, bool kOct, int kMinBlocks>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
   constexpr int kWarps = 8;
-  const size_t smem = (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * kWarps;
-  auto kern = k_transport<R, kWarps, kOct>;
+  const size_t smem = transport_smem<R>();
+  auto kern = k_transport<R, kWarps, kOct, kMinBlocks>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -805,33 +812,36 @@ static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int blocks_per_sm, int sm_count,
-                             cudaStream_t s) {
-  if (kind == 1) {
-    if (precision == 0) return launch_t<double, true>(L, blocks_per_sm, sm_count, s);
-    return launch_t<float, true>(L, blocks_per_sm, sm_count, s);
-  }
-  if (precision == 0) return launch_t<double, false>(L, blocks_per_sm, sm_count, s);
-  return launch_t<float, false>(L, blocks_per_sm, sm_count, s);
-}
-
-template <typename R, bool kOct>
-static int grid_size_t(int blocks_per_sm, int sm_count) {
+template <typename R, bool kOct, int kMinBlocks>
+static int occupancy_t() {
   constexpr int kWarps = 8;
+  auto kern = k_transport<R, kWarps, kOct, kMinBlocks>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem<R>()) != cudaSuccess)
+    return 1;
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transport<R, kWarps, kOct>, kWarps * 32,
-                                                (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * kWarps);
-  if (occ < 1) occ = 1;
-  if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
-  return occ * sm_count;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, transport_smem<R>());
+  return occ < 1 ? 1 : occ;
 }
 
-int transport_grid_size(int precision, int kind, int blocks_per_sm, int sm_count) {
-  if (kind == 1)
-    return precision == 0 ? grid_size_t<double, true>(blocks_per_sm, sm_count)
-                          : grid_size_t<float, true>(blocks_per_sm, sm_count);
-  return precision == 0 ? grid_size_t<double, false>(blocks_per_sm, sm_count)
-                        : grid_size_t<float, false>(blocks_per_sm, sm_count);
+int transport_variants(int precision) { return precision == 0 ? 1 : 2; }
+
+cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
+                             int sm_count, cudaStream_t s) {
+  if (precision == 0) {
+    return kind == 1 ? launch_t<double, true, 1>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<double, false, 1>(L, blocks_per_sm, sm_count, s);
+  }
+  if (variant == 1)
+    return kind == 1 ? launch_t<float, true, 4>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<float, false, 4>(L, blocks_per_sm, sm_count, s);
+  return kind == 1 ? launch_t<float, true, 1>(L, blocks_per_sm, sm_count, s)
+                   : launch_t<float, false, 1>(L, blocks_per_sm, sm_count, s);
+}
+
+int transport_occupancy(int precision, int kind, int variant) {
+  if (precision == 0) return kind == 1 ? occupancy_t<double, true, 1>() : occupancy_t<double, false, 1>();
+  if (variant == 1) return kind == 1 ? occupancy_t<float, true, 4>() : occupancy_t<float, false, 4>();
+  return kind == 1 ? occupancy_t<float, true, 1>() : occupancy_t<float, false, 1>();
 }
 
 }  // namespace colt

@@ -8,6 +8,7 @@ int main(void) {
   printf("colt_run_params %zu\n", sizeof(colt_run_params));
   printf("colt_result %zu\n", sizeof(colt_result));
   printf("colt_stats %zu\n", sizeof(colt_stats));
+  printf("colt_launch_config %zu\n", sizeof(colt_launch_config));
   printf("colt_scatter_io %zu\n", sizeof(colt_scatter_io));
   printf("off_scatter_n_trials %zu\n", offsetof(colt_scatter_io, n_trials));
   printf("off_run_precision %zu\n", offsetof(colt_run_params, precision));

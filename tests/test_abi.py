@@ -54,6 +54,7 @@ def test_binding_struct_layout_matches_header():
     assert sizes["colt_run_params"] == ctypes.sizeof(colt.RunParams)
     assert sizes["colt_result"] == ctypes.sizeof(colt.Result)
     assert sizes["colt_stats"] == ctypes.sizeof(colt.Stats)
+    assert sizes["colt_launch_config"] == ctypes.sizeof(colt.LaunchConfig)
     assert sizes["colt_scatter_io"] == ctypes.sizeof(colt.ScatterIO)
     assert sizes["off_scatter_n_trials"] == colt.ScatterIO.n_trials.offset
     assert sizes["off_run_precision"] == colt.RunParams.precision.offset

@@ -106,3 +106,32 @@ def test_admission_by_memory(colt):
         del st2
     finally:
         colt.colt_finalize(ctx)
+
+
+def test_autotune_keeps_results(colt):
+    # the launch configuration changes only the speed: integer tallies are
+    # bitwise the same under the tuned configuration, blocking and served
+    ctx = colt.colt_init(0)
+    try:
+        g = S.sphere(24, 1e4, 1e5, v_max_kms=100.0, tau_dust=0.5)
+        h = colt.colt_create_grid(ctx, g)
+        sp = S.RunSpec(n_packets=20000, seed=4321, albedo=0.32, spec_units=1, spec_lo=-600, spec_hi=600,
+                       spec_nbins=60, cameras=S.axis_cameras(0), cam_lo=-600, cam_hi=600, cam_nbins=30)
+        before = colt.colt_run(ctx, h, sp)
+        cfg = colt.colt_autotune(ctx, h, sp)
+        assert cfg["variant"] in (0, 1) and cfg["blocks_per_sm"] >= 1 and cfg["scatterings_per_s"] > 0
+        after = colt.colt_run(ctx, h, sp)
+        rid = colt.colt_submit(ctx, h, sp)
+        colt.colt_wait(ctx, rid, timeout_ms=120000)
+        served = colt.colt_read_result(ctx, rid, sp)
+        colt.colt_release(ctx, rid)
+        for r in (after, served):
+            assert np.array_equal(r["spec"], before["spec"])
+            assert r["n_scat"] == before["n_scat"] and r["n_escaped"] == before["n_escaped"]
+            assert np.allclose(r["cam_spec"], before["cam_spec"], rtol=1e-9, atol=1e-300)
+        sp64 = S.RunSpec(**{**sp.__dict__, "precision": 0, "n_packets": 3000})
+        cfg64 = colt.colt_autotune(ctx, h, sp64)
+        assert cfg64["variant"] == 0
+        colt.colt_destroy_grid(ctx, h)
+    finally:
+        colt.colt_finalize(ctx)
