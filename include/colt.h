@@ -204,11 +204,12 @@ typedef struct {
   double scatterings_per_s;  /* measured by colt_autotune */
 } colt_launch_config;
 
-/* Measure short solves of (grid, *params) -- two waves of packets, histories
- * capped at 256 scatterings, no images -- under every configuration the
- * build offers, keep the fastest for params->precision and the grid's kind
- * (every later launch of that pair with blocks_per_sm = 0 uses it, served
- * launches included) and report it in *out (may be NULL).  Blocking. */
+/* Run the solve (grid, *params) -- at most 2^20 packets, no images, the same
+ * packet ids each time -- once under every configuration the build offers,
+ * keep the fastest for params->precision and the grid's kind (every later
+ * launch of that pair with blocks_per_sm = 0 uses it, served launches
+ * included) and report it in *out (may be NULL).  Blocking; costs one solve
+ * per configuration (four for FP32, two for FP64). */
 int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out);
 
 /* Same solve with HOST input fields: builds a temporary grid from desc, runs,

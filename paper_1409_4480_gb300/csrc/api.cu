@@ -1009,16 +1009,17 @@ int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, 
   const int prec = params->precision;
   const int kind = it->second.dev.kind;
   const int gi = prec == COLT_PLAIN ? 0 : 1, gk = kind == COLT_OCTREE ? 1 : 0;
-  // calibration solve: the request's own grid and parameters, two waves of
-  // packets over the largest launch, histories capped at 256 scatterings (the
-  // steady state the configuration decides), no images
+  // calibration: the request itself (at most 2^20 packets, no images), once
+  // per configuration on the same packet ids.  Both what the configuration
+  // trades -- throughput of full warps and the latency of the last, longest
+  // histories -- enter its time, so a heavy-tailed workload is tuned for its
+  // tail and a uniform one for throughput.
   colt_run_params q = *params;
   std::vector<colt_camera> cams(params->cams, params->cams + params->n_cam);
   for (auto& c : cams) c.npix = 0;
   q.cams = cams.data();
   q.blocks_per_sm = 0;
-  q.max_scatter = (q.max_scatter == 0 || q.max_scatter > 256) ? 256 : q.max_scatter;
-  q.n_packets = (uint64_t)ctx->sm_count * 4 * 256 * 2;
+  q.n_packets = std::min<uint64_t>(q.n_packets, 1ull << 20);
   std::vector<uint64_t> spec(q.spec_nbins);
   std::vector<double> cs((size_t)std::max(1, q.n_cam) * q.cam_nbins), cs2(cs.size());
   colt_launch_config best{0, 0, -1.0};
@@ -1027,7 +1028,7 @@ int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, 
     for (int b = occ; b >= std::max(1, occ - 1); --b) {
       ctx->cfg[gi][gk] = colt_launch_config{v, b, 0.0};
       double rate = 0.0;
-      for (int rep = 0; rep < 2; ++rep) {          // the first run warms the configuration up
+      for (int rep = 0; rep < 1; ++rep) {
         colt_result r{};
         r.spec = spec.data();
         if (q.n_cam > 0) {
