@@ -195,9 +195,9 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
 
 /* ------------------------------------------------------------ autotune -- */
 /* Launch configuration of the persistent transport kernel: a register
- * variant (0: the compiler's allocation; 1: registers capped so that four
- * 256-thread CTAs fit on an SM, FP32 only) and the resident CTAs per SM
- * (0 = as many as fit).  The library default is {0, 0}. */
+ * variant (0: the compiler's allocation; 1 / 2: registers capped so that four
+ * / three 256-thread CTAs fit on an SM, FP32 only) and the resident CTAs per
+ * SM (0 = as many as fit).  The library default is {0, 0}. */
 typedef struct {
   int variant;
   int blocks_per_sm;
@@ -209,7 +209,7 @@ typedef struct {
  * keep the fastest for params->precision and the grid's kind (every later
  * launch of that pair with blocks_per_sm = 0 uses it, served launches
  * included) and report it in *out (may be NULL).  Blocking; costs one solve
- * per configuration (four for FP32, two for FP64). */
+ * per configuration (six for FP32, two for FP64). */
 int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out);
 
 /* Same solve with HOST input fields: builds a temporary grid from desc, runs,

@@ -151,8 +151,8 @@ struct LaunchDev {
 // launchers (transport.cu)
 // L is a DEVICE pointer to the launch header (so a captured graph can replay it).
 // All jobs of a launch share one grid kind (COLT_CARTESIAN / COLT_OCTREE).
-// variant: 0 = the compiler's register allocation, 1 = registers capped for
-// four CTAs per SM (FP32 only; transport_variants gives the count);
+// variant: 0 = the compiler's register allocation, 1 / 2 = registers capped
+// for four / three CTAs per SM (FP32 only; transport_variants gives the count);
 // blocks_per_sm 0 = as many CTAs as fit.
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
                              int sm_count, cudaStream_t s);

@@ -117,7 +117,7 @@ __device__ __forceinline__ int64_t cell_index(const GridDev& G, const int c3[3])
 }
 
 // kMinBlocks: resident CTAs per SM the register allocation must allow (1: the
-// compiler's choice, 80 registers and 3 CTAs/SM for FP32; 4: 64 registers)
+// compiler's choice; 3: at most 85 registers; 4: at most 64)
 template <typename R, int kWarps, bool kOct, int kMinBlocks>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_transport(const LaunchDev* __restrict__ Lp) {
@@ -625,6 +625,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       // histories) marches their rays on many lanes at once
       COLT_PHASE(1);
       const unsigned pm = __ballot_sync(kFull, has_peel);
+      if (pm) {   // no event in the warp this round: nothing to peel off
       const int ncl = has_peel ? L.jobs[sev[lane].job].p.n_cam : 0;
       const int ncam_max = (int)__reduce_max_sync(kFull, (unsigned)ncl);
       const int n_pairs = __popc(pm) * ncam_max;
@@ -764,6 +765,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           if (lane == own && !cut) peel_tally(P, e, cam, ax, s, bin, W * m_exp(-tacc));
         }
       }
+      }
     }
     __syncwarp();
     COLT_PHASE(2);
@@ -823,7 +825,7 @@ static int occupancy_t() {
   return occ < 1 ? 1 : occ;
 }
 
-int transport_variants(int precision) { return precision == 0 ? 1 : 2; }
+int transport_variants(int precision) { return precision == 0 ? 1 : 3; }
 
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
                              int sm_count, cudaStream_t s) {
@@ -834,6 +836,9 @@ cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int va
   if (variant == 1)
     return kind == 1 ? launch_t<float, true, 4>(L, blocks_per_sm, sm_count, s)
                      : launch_t<float, false, 4>(L, blocks_per_sm, sm_count, s);
+  if (variant == 2)
+    return kind == 1 ? launch_t<float, true, 3>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<float, false, 3>(L, blocks_per_sm, sm_count, s);
   return kind == 1 ? launch_t<float, true, 1>(L, blocks_per_sm, sm_count, s)
                    : launch_t<float, false, 1>(L, blocks_per_sm, sm_count, s);
 }
@@ -841,6 +846,7 @@ cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int va
 int transport_occupancy(int precision, int kind, int variant) {
   if (precision == 0) return kind == 1 ? occupancy_t<double, true, 1>() : occupancy_t<double, false, 1>();
   if (variant == 1) return kind == 1 ? occupancy_t<float, true, 4>() : occupancy_t<float, false, 4>();
+  if (variant == 2) return kind == 1 ? occupancy_t<float, true, 3>() : occupancy_t<float, false, 3>();
   return kind == 1 ? occupancy_t<float, true, 1>() : occupancy_t<float, false, 1>();
 }
 

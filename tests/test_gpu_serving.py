@@ -119,7 +119,7 @@ def test_autotune_keeps_results(colt):
                        spec_nbins=60, cameras=S.axis_cameras(0), cam_lo=-600, cam_hi=600, cam_nbins=30)
         before = colt.colt_run(ctx, h, sp)
         cfg = colt.colt_autotune(ctx, h, sp)
-        assert cfg["variant"] in (0, 1) and cfg["blocks_per_sm"] >= 1 and cfg["scatterings_per_s"] > 0
+        assert cfg["variant"] in (0, 1, 2) and cfg["blocks_per_sm"] >= 1 and cfg["scatterings_per_s"] > 0
         after = colt.colt_run(ctx, h, sp)
         rid = colt.colt_submit(ctx, h, sp)
         colt.colt_wait(ctx, rid, timeout_ms=120000)
