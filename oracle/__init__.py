@@ -58,7 +58,7 @@ class Result(C.Structure):
                 ("spec_under", C.c_uint64), ("spec_over", C.c_uint64),
                 ("spec", C.c_void_p), ("cam_spec", C.c_void_p), ("cam_spec2", C.c_void_p),
                 ("cam_image", C.c_void_p), ("cam_total", C.c_void_p),
-                ("n_threads_used", C.c_int), ("seconds", C.c_double)]
+                ("n_threads_used", C.c_int), ("seconds", C.c_double), ("transport_seconds", C.c_double)]
 
 
 class ScatterIO(C.Structure):
@@ -288,5 +288,6 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
                n_capped=r.n_capped, n_scat=r.n_scat, n_scat_hi=r.n_scat_hi,
                n_cell_visits=r.n_cell_visits, n_peel_visits=r.n_peel_visits,
                spec_under=r.spec_under, spec_over=r.spec_over, seconds=r.seconds,
+               transport_seconds=r.transport_seconds,
                n_threads=r.n_threads_used)
     return out

@@ -150,7 +150,8 @@ typedef struct {
   double*   cam_image;      /* [n_cam][npix][npix][cam_nbins]     (nullable)   */
   double*   cam_total;      /* [n_cam] sum of all peel-off weights (nullable)  */
   int       n_threads_used;
-  double    seconds;
+  double    seconds;            /* whole call: grid derivation, a tau_NL, packets */
+  double    transport_seconds;  /* the packet loop alone                          */
 } o_result;
 
 /* Non-local a*tau estimate per cell (Eq. atauNL); out has n_cells entries. */
