@@ -407,6 +407,11 @@ def octree_workload(name):
         g = S.halo()
         return g, [((0.0, 0.0, 0.0), 100.0 * S.PC_CM)], S.axis_cameras(128), 200, \
             f"halo_octree_{g.n_cells}leaves_6cam"
+    if name == "halo_diffuse":
+        # the same halo emitting from its gas (recombination + collisional
+        # excitation per leaf): one diffuse source
+        g = S.halo(emission=True)
+        return g, [None], S.axis_cameras(128), 200, f"halo_octree_{g.n_cells}leaves_diffuse_6cam"
     g, src = S.cosmo_box()
     return g, [(p, 0.0) for p in src], S.axis_cameras(512, ("+x", "+y", "+z")), 256, \
         f"cosmo_octree_{g.n_cells}leaves_5src_3cam"
@@ -426,12 +431,14 @@ def run_octree(args):
 
     def specs_of(s):
         out = []
-        for j, (pos, sig) in enumerate(srcs):
+        for j, src in enumerate(srcs):
             off = ((s * world + rank) * len(srcs) + j) * B
+            pos, sig = src if src is not None else ((0.0, 0.0, 0.0), 0.0)
             out.append(S.RunSpec(n_packets=B, seed=300 + j, src_pos=pos, src_sigma=sig, albedo=0.32,
                                  spec_units=1, spec_lo=-1000.0, spec_hi=1000.0, spec_nbins=200, cameras=cams,
                                  cam_units=1, cam_lo=-1000.0, cam_hi=1000.0, cam_nbins=cnb, precision=1,
-                                 pid_offset=off))
+                                 pid_offset=off, source=0 if src is not None else 1,
+                                 core_skip=args.core_skip))
         return out
 
     def run_steps(s0, n):
@@ -463,6 +470,7 @@ def run_octree(args):
             "served_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                   "n_requests": len(lat)},
             "config": {"workload": label, "packets_per_source_per_step": B, "sources": len(srcs),
+                       "core_skip": ["off", "cell + non-local a tau", "Jeans a tau"][args.core_skip],
                        "grid": f"octree, {g.n_cells} leaves, levels {int(g.leaf_level.min())}-{int(g.leaf_level.max())}",
                        "precision": "mixed (FP32 transport, FP32-pair position and tau, FP64 escape)",
                        "l2": "records + tallies exceed the 129 MB L2"},
@@ -589,7 +597,10 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="colt", choices=["colt", "reference"])
-    ap.add_argument("--workload", default="sphere128", choices=["sphere128", "halo", "cosmo", "serving"])
+    ap.add_argument("--workload", default="sphere128",
+                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving"])
+    ap.add_argument("--core-skip", type=int, default=1, choices=[0, 1, 2],
+                    help="octree workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.75)
     ap.add_argument("--packets-per-case", type=int, default=125000)
@@ -609,7 +620,7 @@ def main():
         run_reference(args)
     elif args.single_case >= 0:
         run_single_case(args)
-    elif args.workload in ("halo", "cosmo"):
+    elif args.workload in ("halo", "halo_diffuse", "cosmo"):
         run_octree(args)
     elif args.workload == "serving":
         run_serving(args)

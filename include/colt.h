@@ -53,6 +53,14 @@ enum { COLT_PLAIN = 0, COLT_MIXED = 1 };          /* arithmetic of the transport
 enum { COLT_PHASE_DIPOLE = 0, COLT_PHASE_ISOTROPIC = 1 };
 enum { COLT_UNITS_X = 0, COLT_UNITS_DV_KMS = 1 };
 enum { COLT_EMIT_LINE_CENTRE = 0, COLT_EMIT_NATURAL_THERMAL = 1 };   /* Sec. 3.1.1 */
+/* a tau_0 for the core-skipping cutoff x_crit (Sec. 3.2.4, Eq. xcrit):
+ *   COLT_SKIP_CELL_NL  a tau_cell + a tau_NL (Eqs. atau0min, atauNL);
+ *   COLT_SKIP_JEANS    the Jeans estimate of the scattering cell,
+ *                      a tau_J = 6.428e4 T_4^(-1/2) (n_HI / cm^-3)^(1/2) (Eq. atau0J). */
+enum { COLT_SKIP_OFF = 0, COLT_SKIP_CELL_NL = 1, COLT_SKIP_JEANS = 2 };
+/* where packets are born (Sec. 3.1.1): a point (optionally Gaussian-spread)
+ * source, or the gas itself with a per-cell luminosity (colt_set_cell_luminosity) */
+enum { COLT_SOURCE_POINT = 0, COLT_SOURCE_CELLS = 1 };
 
 /* ------------------------------------------------------------- context -- */
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds what the
@@ -108,6 +116,19 @@ int colt_destroy_grid(colt_ctx* ctx, colt_grid grid);
  * (k_HI = n_HI sigma_0 [cm^-1], a, k_dust [cm^-1], 1/v_th [s/km],
  *  u_x, u_y, u_z [v/v_th], a tau_NL).  n_floats must be 8 * n_cells. */
 int colt_read_cells(colt_ctx* ctx, colt_grid grid, float* out, size_t n_floats);
+/* Diffuse emission (Sec. 3.1.1: recombination and collisional excitation in the
+ * gas; the collisional emissivity of Sec. 5.3): lum[n_cells] is each cell's luminosity (FP64,
+ * any unit; finite, >= 0, not all zero) in host or device memory per mem.  A
+ * packet of a COLT_SOURCE_CELLS run starts in cell c with probability
+ * w_c / sum(w), where w_c = floor(2^s lum_c / max(lum)) and
+ * s = 63 - ceil(log2(n_cells + 1)) (so the weights sum below 2^63 and a cell
+ * below 2^-s of the brightest does not emit), at a uniform position inside it
+ * and an isotropic direction.  The cell is chosen exactly: t = floor(r w_tot
+ * 2^-64) from a 64-bit Philox word r, then the first c whose inclusive prefix
+ * sum of w exceeds t.  The library keeps the prefix sums on the device
+ * (8 bytes per cell, plus 12 per leaf of an octree); a second call replaces
+ * the first.  COLT_EINVAL for bad values, COLT_ENOMEM over the budget. */
+int colt_set_cell_luminosity(colt_ctx* ctx, colt_grid grid, const double* lum, int mem);
 
 /* ------------------------------------------------------------------ runs -- */
 /* A distant observer along a coordinate axis (Sec. 6.1: six axis cameras).
@@ -123,7 +144,8 @@ typedef struct {
   uint64_t seed;            /* Philox key; results depend only on (seed, packet id) */
   double src_pos[3];        /* point source position (cm)                            */
   double src_sigma;         /* Gaussian spread of the source (cm), 0 = point          */
-  int core_skip;            /* Sec. 3.2.4                                             */
+  int core_skip;            /* COLT_SKIP_* (Sec. 3.2.4); any other nonzero value is
+                               rejected                                             */
   int recoil;               /* Eq. recoil                                             */
   int phase;                /* COLT_PHASE_DIPOLE (Eq. phaseW) or _ISOTROPIC           */
   double tau_esc_max;       /* peel-off cutoff, 50 in Sec. 6.1                        */
@@ -152,6 +174,9 @@ typedef struct {
                                COLT_EMIT_NATURAL_THERMAL: x = x_nat + k.u_atom with a
                                Lorentzian x_nat (width a) and a Maxwellian atom velocity
                                of the source cell (Sec. 3.1.1)                      */
+  int source;               /* COLT_SOURCE_POINT (src_pos, src_sigma) or
+                               COLT_SOURCE_CELLS (the grid's cell luminosities;
+                               src_pos and src_sigma unused)                        */
 } colt_run_params;
 
 /* Outputs of a run.  Counters are always filled; every array pointer may be

@@ -31,7 +31,8 @@ class GridIn(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic_xy", C.c_int),
                 ("n_HI", C.c_void_p), ("T", C.c_void_p), ("vx", C.c_void_p), ("vy", C.c_void_p),
                 ("vz", C.c_void_p), ("k_dust", C.c_void_p),
-                ("n_leaves", C.c_int64), ("leaf_level", C.c_void_p), ("leaf_ijk", C.c_void_p)]
+                ("n_leaves", C.c_int64), ("leaf_level", C.c_void_p), ("leaf_ijk", C.c_void_p),
+                ("lum", C.c_void_p)]
 
 
 class Camera(C.Structure):
@@ -48,7 +49,7 @@ class Params(C.Structure):
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double),
                 ("cam_nbins", C.c_int), ("fov_half", C.c_double), ("n_threads", C.c_int),
                 ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p),
-                ("pid0", C.c_uint64), ("emission", C.c_int)]
+                ("pid0", C.c_uint64), ("emission", C.c_int), ("source", C.c_int)]
 
 
 class Result(C.Structure):
@@ -75,6 +76,8 @@ def _setup(L):
                  "o_x_cw_lambert", "o_x_crit"):
         getattr(L, name).restype = d
         getattr(L, name).argtypes = [d]
+    L.o_atau_jeans.restype = d
+    L.o_atau_jeans.argtypes = [d, d]
     for name in ("o_H_exact", "o_H_approx"):
         getattr(L, name).restype = d
         getattr(L, name).argtypes = [d, d]
@@ -111,6 +114,9 @@ def recoil_g(T): return lib().o_recoil_g(float(T))
 def x_cw_fit(a): return lib().o_x_cw_fit(float(a))
 def x_cw_lambert(a): return lib().o_x_cw_lambert(float(a))
 def x_crit(atau0): return lib().o_x_crit(float(atau0))
+
+
+def atau_jeans(T, n_HI): return lib().o_atau_jeans(float(T), float(n_HI))
 
 
 def _vec2(fn, a, x):
@@ -208,6 +214,7 @@ def _grid_struct(g):
         s.n_leaves = int(g.n_cells)
         s.leaf_level = P(g.leaf_level, np.uint8)
         s.leaf_ijk = P(g.leaf_ijk, np.uint32)
+    s.lum = P(getattr(g, "lum", None), np.float64)
     return s, keep
 
 
@@ -237,7 +244,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     p.seed = int(spec.seed)
     p.src_pos = (C.c_double * 3)(*[float(v) for v in spec.src_pos])
     p.src_sigma = float(spec.src_sigma)
-    p.core_skip = int(bool(spec.core_skip))
+    p.core_skip = int(spec.core_skip)
     p.recoil = int(bool(spec.recoil))
     p.phase = int(spec.phase)
     p.f_nl = float(spec.f_nl)
@@ -245,6 +252,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     p.albedo = float(spec.albedo)
     p.max_scatter = int(spec.max_scatter)
     p.emission = int(getattr(spec, "emission", 0) or 0)
+    p.source = int(getattr(spec, "source", 0) or 0)
     p.spec_units = int(spec.spec_units)
     p.T_ref = float(spec.T_ref)
     p.spec_lo, p.spec_hi, p.spec_nbins = float(spec.spec_lo), float(spec.spec_hi), int(spec.spec_nbins)

@@ -35,7 +35,7 @@
 
 static void free_all(o_grid* g) {
   free(g->kHI); free(g->a); free(g->vth); free(g->u); free(g->kd); free(g->g);
-  free(g->nHI); free(g->atau_nl); free(g->child); free(g->node_leaf);
+  free(g->nHI); free(g->atau_nl); free(g->T); free(g->child); free(g->node_leaf);
   free(g->lev); free(g->ijk);
   memset(g, 0, sizeof(*g));
 }
@@ -124,7 +124,8 @@ int o_grid_build(const o_grid_in* in, o_grid* g) {
   g->g = (double*)malloc((size_t)n * sizeof(double));
   g->nHI = (double*)malloc((size_t)n * sizeof(double));
   g->atau_nl = (double*)calloc((size_t)n, sizeof(double));
-  if (!g->kHI || !g->a || !g->vth || !g->u || !g->kd || !g->g || !g->nHI || !g->atau_nl) {
+  g->T = (double*)malloc((size_t)n * sizeof(double));
+  if (!g->kHI || !g->a || !g->vth || !g->u || !g->kd || !g->g || !g->nHI || !g->atau_nl || !g->T) {
     free_all(g);
     return -2;
   }
@@ -133,6 +134,7 @@ int o_grid_build(const o_grid_in* in, o_grid* g) {
     if (!(T > 0.0) || !(in->n_HI[c] >= 0.0)) { free_all(g); return -1; }
     double vth = o_vth_kms(T);
     g->nHI[c] = in->n_HI[c];
+    g->T[c] = T;
     g->kHI[c] = (double)in->n_HI[c] * o_sigma0(T);          /* Eq. tauH */
     g->a[c] = o_damping_a(T);
     g->vth[c] = vth;

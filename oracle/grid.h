@@ -10,7 +10,7 @@ typedef struct {
   int periodic_xy;
   int64_t n_cells;
   /* derived per-cell quantities, FP64 */
-  double *kHI, *a, *vth, *u, *kd, *g, *nHI, *atau_nl;
+  double *kHI, *a, *vth, *u, *kd, *g, *nHI, *atau_nl, *T;
   /* octree */
   int64_t n_nodes;
   int max_level;

@@ -37,6 +37,7 @@ void   o_H_exact_many(const double* a, const double* x, double* H, size_t n);
 double o_x_cw_fit(double a);            /* Sec. 3.2.2, Eq. xcw (rational fit)    */
 double o_x_cw_lambert(double a);        /* Sec. 3.2.2, Eq. xcw (W_{-1} solution) */
 double o_x_crit(double atau0);          /* Sec. 3.2.4, Eq. xcrit                 */
+double o_atau_jeans(double T, double n_HI);  /* Sec. 3.2.4, Eq. atau0J (n in cm^-3) */
 
 /* ----------------------------------------------------------------- RNG -- */
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), counter-based. */
@@ -96,6 +97,8 @@ typedef struct {
   int64_t n_leaves;
   const uint8_t*  leaf_level;
   const uint32_t* leaf_ijk;  /* 3 per leaf */
+  /* per-cell luminosity for diffuse emission (source = 1), may be NULL       */
+  const double* lum;
 } o_grid_in;
 
 typedef struct {
@@ -108,7 +111,8 @@ typedef struct {
   uint64_t seed;
   double   src_pos[3];      /* cm */
   double   src_sigma;       /* Gaussian spread of the source (cm), 0 = point   */
-  int      core_skip;       /* Sec. 3.2.4 on/off                               */
+  int      core_skip;       /* Sec. 3.2.4: 0 off, 1 a tau_cell + a tau_NL,
+                               2 a tau_J of the scattering cell (Eq. atau0J)   */
   int      recoil;          /* Eq. recoil on/off                               */
   int      phase;           /* 0 dipole (Eq. phaseW), 1 isotropic              */
   double   f_nl;            /* non-local threshold, Eq. atauNL                 */
@@ -135,6 +139,7 @@ typedef struct {
                                max_scatter the lab frequency at the cap        */
   uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
   int       emission;       /* 0 line centre (x = 0), 1 natural + thermal        */
+  int       source;         /* 0 point (src_pos, src_sigma), 1 cells by luminosity */
 } o_params;
 
 typedef struct {

@@ -5,7 +5,11 @@
  *                               allows it for optically thick media)
  *   Sec. 3.1.2, Eq. lnR       : tau_event = -ln R, cell-by-cell walk, Eq. tauH
  *   Sec. 3.1.3                : scattering (see scatter.c)
- *   Sec. 3.2.4                : a tau_0 = a tau_cell + a tau_NL, Eq. atau0min
+ *   Sec. 3.2.4                : a tau_0 = a tau_cell + a tau_NL, Eq. atau0min,
+ *                               or the Jeans estimate a tau_J, Eq. atau0J
+ *   Sec. 3.1.1                : diffuse emission from the gas: a cell drawn
+ *                               with probability proportional to its
+ *                               (quantised) luminosity, a uniform position in it
  *   Sec. 6.1, Eq. SB          : next-event (peel-off) estimator, sum of
  *                               W(theta) exp(-tau_esc), traced only while
  *                               tau_esc <= tau_esc_max (50 in the paper)
@@ -31,7 +35,9 @@
  *   - a flight that visits more than 2^24 cells (only possible on periodic
  *     grids with empty cells) ends the packet as capped.
  * RNG: event 0 is the emission (block 0: mu, phi, tau_event; block 1: source
- * Gaussian); event e >= 1 is the e-th interaction, blocks as in scatter.c.
+ * Gaussian, or for diffuse emission words 0-1 as one 64-bit number choosing
+ * the cell; block 3: the position in that cell); event e >= 1 is the e-th
+ * interaction, blocks as in scatter.c.
  */
 #include "grid.h"
 #include <math.h>
@@ -66,6 +72,9 @@ typedef struct {
   int64_t img_n;
   int64_t* img_idx;
   double* img_w;
+  /* diffuse emission: inclusive prefix sums of the cell weights, and their total */
+  const uint64_t* lum_cum;
+  uint64_t lum_total;
 } worker;
 
 static void draw_block(const uint32_t key[2], uint64_t pid, uint32_t event, uint32_t blk, double u[4]) {
@@ -193,18 +202,39 @@ static void run_packet(worker* w, uint64_t idx) {
   double k[3] = {st * cos(phi), st * sin(phi), mu};
   double tau = -log(B0[2]);
   double r[3] = {p->src_pos[0], p->src_pos[1], p->src_pos[2]};
-  if (p->src_sigma > 0.0) {
-    draw_block(w->key, pid, 0, 1, B1);
-    double rho1 = sqrt(-2.0 * log(B1[0])), rho2 = sqrt(-2.0 * log(B1[2]));
-    r[0] += p->src_sigma * rho1 * cos(2.0 * O_PI * B1[1]);
-    r[1] += p->src_sigma * rho1 * sin(2.0 * O_PI * B1[1]);
-    r[2] += p->src_sigma * rho2 * cos(2.0 * O_PI * B1[3]);
+  int64_t c;
+  if (p->source == 1) {
+    /* diffuse emission: t uniform on [0, W) from the 64-bit word (block 1,
+     * words 0 and 1) as floor(word W / 2^64); the cell is the first whose
+     * inclusive prefix weight exceeds t; the position is uniform inside it */
+    uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 1u}, q[4];
+    o_philox4x32_10(ctr, w->key, q);
+    uint64_t word = ((uint64_t)q[1] << 32) | q[0];
+    uint64_t t = (uint64_t)(((unsigned __int128)word * w->lum_total) >> 64);
+    int64_t lo = 0, hi = g->n_cells - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      if (w->lum_cum[mid] > t) hi = mid; else lo = mid + 1;
+    }
+    c = lo;
+    double B3[4], clo[3], chi[3];
+    draw_block(w->key, pid, 0, 3, B3);
+    o_cell_bounds(g, c, clo, chi);
+    for (int i = 0; i < 3; ++i) r[i] = clo[i] + B3[i] * (chi[i] - clo[i]);
+  } else {
+    if (p->src_sigma > 0.0) {
+      draw_block(w->key, pid, 0, 1, B1);
+      double rho1 = sqrt(-2.0 * log(B1[0])), rho2 = sqrt(-2.0 * log(B1[2]));
+      r[0] += p->src_sigma * rho1 * cos(2.0 * O_PI * B1[1]);
+      r[1] += p->src_sigma * rho1 * sin(2.0 * O_PI * B1[1]);
+      r[2] += p->src_sigma * rho2 * cos(2.0 * O_PI * B1[3]);
+    }
+    c = o_locate_cell(g, r, k);
   }
   double x = 0.0;
   uint64_t nscat = 0;
   int status = 0;
   double s_esc = 0.0;
-  int64_t c = o_locate_cell(g, r, k);
   if (c < 0) {
     /* source outside the domain: leaves at once, at line centre */
     status = 1;
@@ -280,7 +310,12 @@ static void run_packet(worker* w, uint64_t idx) {
       for (int i = 0; i < 3; ++i) s.k[i] = k[i];
       s.a = g->a[c];
       s.g = p->recoil ? g->g[c] : 0.0;
-      s.atau0 = p->core_skip ? g->a[c] * g->kHI[c] * o_min_face_distance(g, c, r) + g->atau_nl[c] : -1.0;
+      if (p->core_skip == 2)
+        s.atau0 = o_atau_jeans(g->T[c], g->nHI[c]);
+      else if (p->core_skip)
+        s.atau0 = g->a[c] * g->kHI[c] * o_min_face_distance(g, c, r) + g->atau_nl[c];
+      else
+        s.atau0 = -1.0;
       s.phase = p->phase;
       s.pid = pid;
       s.event = event;
@@ -341,7 +376,32 @@ int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
   o_grid g;
   int rc = o_grid_build(gin, &g);
   if (rc) return rc;
-  if (p->core_skip) o_atau_nl_grid(&g, p->f_nl);
+  if (p->core_skip == 1) o_atau_nl_grid(&g, p->f_nl);
+  /* diffuse emission: integer weights w_c = floor(2^s L_c / max L) with
+   * s = 63 - b, b the least integer with 2^b >= n_cells + 1 (the weights then
+   * sum below 2^63), and their inclusive prefix sums */
+  uint64_t* lum_cum = NULL;
+  uint64_t lum_total = 0;
+  if (p->source == 1) {
+    int64_t n = g.n_cells;
+    if (!gin->lum) { o_grid_free(&g); return -1; }
+    double lmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!(gin->lum[i] >= 0.0) || !isfinite(gin->lum[i])) { o_grid_free(&g); return -1; }
+      if (gin->lum[i] > lmax) lmax = gin->lum[i];
+    }
+    if (!(lmax > 0.0)) { o_grid_free(&g); return -1; }
+    int b = 0;
+    while (b < 63 && ((uint64_t)1 << b) < (uint64_t)n + 1) ++b;
+    lum_cum = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    for (int64_t i = 0; i < n; ++i) {
+      lum_total += (uint64_t)floor(ldexp(gin->lum[i] / lmax, 63 - b));
+      lum_cum[i] = lum_total;
+    }
+  } else if (p->source != 0) {
+    o_grid_free(&g);
+    return -1;
+  }
   struct timespec tm;
   clock_gettime(CLOCK_MONOTONIC, &tm);
   int nt = p->n_threads;
@@ -358,6 +418,7 @@ int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
     w->key[0] = (uint32_t)p->seed; w->key[1] = (uint32_t)(p->seed >> 32);
     w->vth_ref = o_vth_kms(p->T_ref > 0.0 ? p->T_ref : 1.0e4);
     w->tid = t; w->nthreads = nt; w->img_lock = &lock;
+    w->lum_cum = lum_cum; w->lum_total = lum_total;
     w->spec = (uint64_t*)calloc((size_t)p->spec_nbins, sizeof(uint64_t));
     if (ncs) {
       w->cam_spec = (double*)calloc(ncs, sizeof(double));
@@ -399,6 +460,7 @@ int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
     free(w->img_idx); free(w->img_w);
   }
   free(ws); free(th);
+  free(lum_cum);
   pthread_mutex_destroy(&lock);
   o_grid_free(&g);
   clock_gettime(CLOCK_MONOTONIC, &t1);

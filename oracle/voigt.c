@@ -183,6 +183,12 @@ double o_x_cw_lambert(double a) {
   return sqrt(-lambert_wm1(-a / O_SQRTPI));
 }
 
+/* Sec. 3.2.4, Eq. atau0J: the local a tau_0 of a uniform region one Jeans
+ * length across (primordial gas, mu = 1.23 m_H, X = 0.75). */
+double o_atau_jeans(double T, double n_HI) {
+  return 6.428e4 / sqrt(T / 1.0e4) * sqrt(n_HI);
+}
+
 /* Sec. 3.2.4, Eq. xcrit. */
 double o_x_crit(double atau0) {
   if (atau0 < 1.0) return 0.0;

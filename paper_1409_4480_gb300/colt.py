@@ -24,11 +24,13 @@ COLT_OK, COLT_EINVAL, COLT_ENOMEM, COLT_EAGAIN, COLT_ETIMEOUT, COLT_ECUDA, COLT_
 COLT_CARTESIAN, COLT_OCTREE = 0, 1
 COLT_MEM_HOST, COLT_MEM_DEVICE = 0, 1
 COLT_PLAIN, COLT_MIXED = 0, 1
+COLT_SKIP_OFF, COLT_SKIP_CELL_NL, COLT_SKIP_JEANS = 0, 1, 2
+COLT_SOURCE_POINT, COLT_SOURCE_CELLS = 0, 1
 
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
            "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
-           "colt_run_noalloc", "colt_autotune"]
+           "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity"]
 
 _LIB = None
 
@@ -59,7 +61,8 @@ class RunParams(C.Structure):
                 ("spec_hi", C.c_double), ("spec_nbins", C.c_int), ("n_cam", C.c_int), ("cams", C.c_void_p),
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double), ("cam_nbins", C.c_int),
                 ("fov_half", C.c_double), ("precision", C.c_int), ("block_size", C.c_int),
-                ("blocks_per_sm", C.c_int), ("pid_offset", C.c_uint64), ("emission", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("pid_offset", C.c_uint64), ("emission", C.c_int),
+                ("source", C.c_int)]
 
 
 class Result(C.Structure):
@@ -131,6 +134,7 @@ def lib():
             "colt_scatter": (I, [P, P, SZ, U64, I]),
             "colt_run_noalloc": (I, [I, P, P, P, P]),
             "colt_autotune": (I, [P, U64, P, P]),
+            "colt_set_cell_luminosity": (I, [P, U64, P, I]),
         }
         for name, (rt, args) in sig.items():
             f = getattr(L, name)
@@ -218,10 +222,29 @@ def grid_desc(grid, f_nl: float = 0.5, device_fields=None):
 
 
 def colt_create_grid(ctx, grid, f_nl: float = 0.5, device_fields=None) -> int:
+    """Create the device grid; a synth.Grid carrying cell luminosities
+    (grid.lum) also gets them set (colt_set_cell_luminosity)."""
     d, keep = grid_desc(grid, f_nl, device_fields)
     h = C.c_uint64()
     _check(ctx, lib().colt_create_grid(ctx, C.byref(d), C.byref(h)))
+    if getattr(grid, "lum", None) is not None:
+        try:
+            colt_set_cell_luminosity(ctx, h.value, grid.lum)
+        except ColtError:
+            lib().colt_destroy_grid(ctx, h)
+            raise
     return h.value
+
+
+def colt_set_cell_luminosity(ctx, grid: int, lum):
+    """lum: per-cell luminosities, a float64 numpy array (host) or a CUDA
+    torch tensor of float64 (device)."""
+    if hasattr(lum, "data_ptr"):
+        _check(ctx, lib().colt_set_cell_luminosity(ctx, C.c_uint64(grid), C.c_void_p(lum.data_ptr()),
+                                                   COLT_MEM_DEVICE))
+    else:
+        a = np.ascontiguousarray(lum, np.float64)
+        _check(ctx, lib().colt_set_cell_luminosity(ctx, C.c_uint64(grid), _ptr(a), COLT_MEM_HOST))
 
 
 def colt_destroy_grid(ctx, grid: int):
@@ -241,7 +264,7 @@ def run_params(spec, images: bool = False):
     p.seed = int(spec.seed)
     p.src_pos = (C.c_double * 3)(*[float(v) for v in spec.src_pos])
     p.src_sigma = float(spec.src_sigma)
-    p.core_skip = int(bool(spec.core_skip))
+    p.core_skip = int(spec.core_skip)
     p.recoil = int(bool(spec.recoil))
     p.phase = int(spec.phase)
     p.tau_esc_max = float(spec.tau_esc_max)
@@ -265,6 +288,7 @@ def run_params(spec, images: bool = False):
     p.blocks_per_sm = int(getattr(spec, "blocks_per_sm", 0) or 0)
     p.pid_offset = int(getattr(spec, "pid_offset", 0) or 0)
     p.emission = int(getattr(spec, "emission", 0) or 0)
+    p.source = int(getattr(spec, "source", 0) or 0)
     return p, cams
 
 

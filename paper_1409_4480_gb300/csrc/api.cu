@@ -46,6 +46,11 @@ struct GridObj {
   float4* rec = nullptr;
   int32_t* node = nullptr;              // octree: node table (device)
   uint32_t* nbr = nullptr;              // octree: face neighbours (device)
+  unsigned long long* lum_cum = nullptr;  // diffuse emission: prefix sums of the cell weights (device)
+  uint32_t* leaf_loc = nullptr;         // octree + diffuse emission: leaf level and coordinates (device)
+  size_t lum_bytes = 0;
+  std::vector<uint8_t> leaf_level;      // octree leaves (host copies)
+  std::vector<uint32_t> leaf_ijk;
   size_t bytes = 0;
   // longest history (scatterings) any finished solve on this grid has had
   uint64_t longest = 0;
@@ -179,7 +184,12 @@ int camera_axis(const double d[3], int* axis, int* sgn) {
   return 0;
 }
 
-int validate_params(colt_ctx* ctx, const colt_run_params* p) {
+int validate_params(colt_ctx* ctx, const colt_run_params* p, const GridObj& g) {
+  if (p->core_skip != COLT_SKIP_OFF && p->core_skip != COLT_SKIP_CELL_NL && p->core_skip != COLT_SKIP_JEANS)
+    return fail(ctx, COLT_EINVAL, "bad core_skip mode");
+  if (p->source != COLT_SOURCE_POINT && p->source != COLT_SOURCE_CELLS) return fail(ctx, COLT_EINVAL, "bad source");
+  if (p->source == COLT_SOURCE_CELLS && !g.lum_cum)
+    return fail(ctx, COLT_EINVAL, "COLT_SOURCE_CELLS needs colt_set_cell_luminosity on the grid");
   if (!p) return fail(ctx, COLT_EINVAL, "params is NULL");
   if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo)) return fail(ctx, COLT_EINVAL, "bad escape-spectrum bins");
   if (p->n_cam < 0 || p->n_cam > kMaxCams) return fail(ctx, COLT_EINVAL, "n_cam must be in [0, 8]");
@@ -265,10 +275,13 @@ RunDev make_run(const GridObj& g, const colt_run_params* p) {
   r.rng = Rng{uint32_t(p->seed), uint32_t(p->seed >> 32)};
   for (int a = 0; a < 3; ++a) r.src[a] = p->src_pos[a];
   r.src_sigma = p->src_sigma;
-  r.core_skip = p->core_skip ? 1 : 0;
+  r.core_skip = p->core_skip;
   r.recoil = p->recoil ? 1 : 0;
   r.phase = p->phase;
   r.emission = p->emission;
+  r.source = p->source;
+  r.jeans_c = jeans_coefficient();
+  r.jeans_cf = (float)r.jeans_c;
   r.tau_max = p->tau_esc_max;
   r.albedo = p->albedo;
   r.max_scatter = p->max_scatter;
@@ -538,6 +551,8 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
   if (oct) {
     int rc = build_octree_tables(ctx, n, d->leaf_level, d->leaf_ijk, &node, &nbr, &max_level);
     if (rc) return rc;
+    g->leaf_level.assign(d->leaf_level, d->leaf_level + n);
+    g->leaf_ijk.assign(d->leaf_ijk, d->leaf_ijk + 3 * n);
   }
   const size_t bytes = sizeof(float4) * 2 * (size_t)n + sizeof(int32_t) * node.size() + sizeof(uint32_t) * nbr.size();
   if (ctx->used + bytes > ctx->budget) return fail(ctx, COLT_ENOMEM, "grid exceeds the memory budget");
@@ -608,9 +623,13 @@ void free_grid(GridObj& g) {
   if (g.rec) cudaFree(g.rec);
   if (g.node) cudaFree(g.node);
   if (g.nbr) cudaFree(g.nbr);
+  if (g.lum_cum) cudaFree(g.lum_cum);
+  if (g.leaf_loc) cudaFree(g.leaf_loc);
   g.rec = nullptr;
   g.node = nullptr;
   g.nbr = nullptr;
+  g.lum_cum = nullptr;
+  g.leaf_loc = nullptr;
 }
 
 // Record the longest history a finished job saw on its grid.
@@ -915,6 +934,82 @@ int colt_read_cells(colt_ctx* ctx, colt_grid grid, float* out, size_t n_floats) 
   return COLT_OK;
 }
 
+int colt_set_cell_luminosity(colt_ctx* ctx, colt_grid grid, const double* lum, int mem) {
+  if (!ctx || !lum) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  auto it = ctx->grids.find(grid);
+  if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
+  if (mem != COLT_MEM_HOST && mem != COLT_MEM_DEVICE) return fail(ctx, COLT_EINVAL, "bad mem");
+  for (auto& kv : ctx->reqs)
+    if (kv.second->grid == grid && kv.second->state != kDone)
+      return fail(ctx, COLT_EINVAL, "grid is in use by an unfinished request");
+  GridObj& g = it->second;
+  const int64_t n = g.dev.n_cells;
+  const bool oct = g.dev.kind == COLT_OCTREE;
+  std::vector<double> hl;
+  const double* L = lum;
+  if (mem == COLT_MEM_DEVICE) {
+    hl.resize(n);
+    CU(cudaMemcpyAsync(hl.data(), lum, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    L = hl.data();
+  }
+  // integer weights w_c = floor(2^s lum_c / max lum), s = 63 - ceil(log2(n + 1)):
+  // their sum stays below 2^63 and the prefix sums are exact in any order
+  double lmax = 0.0;
+  for (int64_t c = 0; c < n; ++c) {
+    if (!(L[c] >= 0) || !std::isfinite(L[c])) return fail(ctx, COLT_EINVAL, "cell luminosities must be finite and >= 0");
+    lmax = std::max(lmax, L[c]);
+  }
+  if (!(lmax > 0)) return fail(ctx, COLT_EINVAL, "no cell has a positive luminosity");
+  int bits = 0;
+  while (bits < 63 && ((uint64_t)1 << bits) < (uint64_t)n + 1) ++bits;
+  const int s = 63 - bits;
+  std::vector<unsigned long long> cum(n);
+  unsigned long long acc = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    acc += (unsigned long long)std::floor(std::ldexp(L[c] / lmax, s));
+    cum[c] = acc;
+  }
+  const size_t bytes = sizeof(unsigned long long) * (size_t)n + (oct ? sizeof(uint32_t) * 3 * (size_t)n : 0);
+  if (ctx->used - g.lum_bytes + bytes > ctx->budget) return fail(ctx, COLT_ENOMEM, "luminosity table exceeds the memory budget");
+  std::vector<uint32_t> loc;
+  if (oct) {
+    loc.resize(3 * (size_t)n);
+    for (int64_t c = 0; c < n; ++c) {
+      loc[3 * c] = g.leaf_ijk[3 * c] | ((uint32_t)g.leaf_level[c] << 24);
+      loc[3 * c + 1] = g.leaf_ijk[3 * c + 1];
+      loc[3 * c + 2] = g.leaf_ijk[3 * c + 2];
+    }
+  }
+  cudaStreamSynchronize(ctx->stream);
+  if (g.lum_cum) cudaFree(g.lum_cum);
+  if (g.leaf_loc) cudaFree(g.leaf_loc);
+  g.lum_cum = nullptr;
+  g.leaf_loc = nullptr;
+  g.dev.lum_cum = nullptr;
+  g.dev.leaf_loc = nullptr;
+  g.dev.lum_total = 0;
+  ctx->used -= g.lum_bytes;
+  g.bytes -= g.lum_bytes;
+  g.lum_bytes = 0;
+  CU(cudaMalloc(&g.lum_cum, sizeof(unsigned long long) * (size_t)n));
+  CU(cudaMemcpyAsync(g.lum_cum, cum.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+  if (oct) {
+    CU(cudaMalloc(&g.leaf_loc, sizeof(uint32_t) * 3 * (size_t)n));
+    CU(cudaMemcpyAsync(g.leaf_loc, loc.data(), sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  g.dev.lum_cum = g.lum_cum;
+  g.dev.leaf_loc = g.leaf_loc;
+  g.dev.lum_total = acc;
+  g.lum_bytes = bytes;
+  g.bytes += bytes;
+  ctx->used += bytes;
+  return COLT_OK;
+}
+
 int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
                    colt_result* out) {
   if (!ctx || !grids || !params || !out || n < 1 || n > kMaxJobs) return COLT_EINVAL;
@@ -927,7 +1022,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     auto it = ctx->grids.find(grids[i]);
     if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
     gs[i] = &it->second;
-    int rc = validate_params(ctx, &params[i]);
+    int rc = validate_params(ctx, &params[i], *gs[i]);
     if (rc) return rc;
     if (params[i].precision != prec) return fail(ctx, COLT_EINVAL, "all solves of a batch need one precision");
     if (gs[i]->dev.kind != gs[0]->dev.kind) return fail(ctx, COLT_EINVAL, "all solves of a batch need one grid kind");
@@ -1004,7 +1099,7 @@ int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, 
   cudaSetDevice(ctx->device);
   auto it = ctx->grids.find(grid);
   if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
-  int rc = validate_params(ctx, params);
+  int rc = validate_params(ctx, params, it->second);
   if (rc) return rc;
   const int prec = params->precision;
   const int kind = it->second.dev.kind;
@@ -1067,7 +1162,7 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   cudaSetDevice(ctx->device);
   auto it = ctx->grids.find(grid);
   if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
-  int rc = validate_params(ctx, p);
+  int rc = validate_params(ctx, p, it->second);
   if (rc) return rc;
   if (ctx->queue.size() >= 4096) return fail(ctx, COLT_EAGAIN, "request queue full");
   auto r = std::make_unique<Req>();

@@ -1,6 +1,7 @@
 // Internal structures shared by the library's translation units (not part of
 // the public ABI; see include/colt.h for that).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -25,6 +26,12 @@ constexpr uint32_t kNoNbr = 0xFFFFFFFFu;
 constexpr uint32_t kNodeMask = (1u << 27) - 1u;
 constexpr int kMaxOctLevel = 24;
 
+// Eq. atau0J, a tau_J = 6.428e4 T_4^(-1/2) (n_HI / cm^-3)^(1/2), in terms of the
+// cell record: with a = 4.702e-4 T_4^(-1/2) and k_HI = n_HI 5.898e-14 T_4^(-1/2) cm^-1
+// (Sec. 2), a k_HI = 4.702e-4 x 5.898e-14 T_4^-1 n_HI, so a tau_J = C sqrt(a k_HI)
+// with C = 6.428e4 / sqrt(4.702e-4 x 5.898e-14) (cm^1/2).
+inline double jeans_coefficient() { return 6.428e4 / std::sqrt(4.702e-4 * 5.898e-14); }
+
 struct GridDev {
   const float4* rec = nullptr;
   int kind = 0;
@@ -40,6 +47,11 @@ struct GridDev {
   const int32_t* node = nullptr;
   const uint32_t* nbr = nullptr;
   int max_level = 0;
+  // diffuse emission: inclusive prefix sums of the integer cell weights and
+  // their total; octree: per leaf (i | level << 24, j, k)
+  const unsigned long long* lum_cum = nullptr;
+  unsigned long long lum_total = 0;
+  const uint32_t* leaf_loc = nullptr;
 };
 
 struct CamDev {
@@ -81,8 +93,13 @@ struct RunDev {
   Rng rng{0, 0};
   double src[3] = {0, 0, 0};
   double src_sigma = 0;
-  int core_skip = 1, recoil = 1, phase = 0;
+  int core_skip = 1, recoil = 1, phase = 0;   // core_skip: COLT_SKIP_*
   int emission = 0;           // 0 line centre, 1 natural + thermal (Sec. 3.1.1)
+  int source = 0;             // COLT_SOURCE_POINT / COLT_SOURCE_CELLS
+  // a tau_J = jeans_c sqrt(a k_HI) (Eq. atau0J rewritten with a and sigma_0 of
+  // the cell record), in FP64 and FP32
+  double jeans_c = 0;
+  float jeans_cf = 0;
   double tau_max = 50.0;
   double albedo = 0.0;
   uint64_t max_scatter = ~0ull;

@@ -95,6 +95,9 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     if (!gv.records || gv.nx <= 0 || gv.ny <= 0 || gv.nz <= 0) return COLT_EINVAL;
     if (p.precision != precision || (p.precision != COLT_PLAIN && p.precision != COLT_MIXED)) return COLT_EINVAL;
     if (p.emission != COLT_EMIT_LINE_CENTRE && p.emission != COLT_EMIT_NATURAL_THERMAL) return COLT_EINVAL;
+    if (p.core_skip != COLT_SKIP_OFF && p.core_skip != COLT_SKIP_CELL_NL && p.core_skip != COLT_SKIP_JEANS)
+      return COLT_EINVAL;
+    if (p.source != COLT_SOURCE_POINT) return COLT_EINVAL;   // a grid view carries no luminosity table
     if (p.spec_nbins <= 0 || !(p.spec_hi > p.spec_lo) || !t.spec || !t.counters) return COLT_EINVAL;
     if (p.n_cam < 0 || p.n_cam > kMaxCams) return COLT_EINVAL;
     if (p.n_cam > 0 && (!p.cams || p.cam_nbins <= 0 || !(p.cam_hi > p.cam_lo) || !t.cam_spec || !t.cam_spec2))
@@ -124,7 +127,9 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     r.rng = Rng{uint32_t(p.seed), uint32_t(p.seed >> 32)};
     for (int a = 0; a < 3; ++a) r.src[a] = p.src_pos[a];
     r.src_sigma = p.src_sigma;
-    r.core_skip = p.core_skip ? 1 : 0;
+    r.core_skip = p.core_skip;
+    r.jeans_c = jeans_coefficient();
+    r.jeans_cf = (float)r.jeans_c;
     r.recoil = p.recoil ? 1 : 0;
     r.phase = p.phase;
     r.emission = p.emission;

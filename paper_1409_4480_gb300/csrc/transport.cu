@@ -1,11 +1,15 @@
 // Persistent photon-packet transport kernel (Cartesian grids).
 //
 // Paper mapping:
-//   emission           Sec. 3.1.1 (isotropic k_i, x_i = 0 in the source cell)
+//   emission           Sec. 3.1.1 (isotropic k_i, x_i = 0 in the source cell, or
+//                      natural + thermal; a point source, or diffuse emission from
+//                      cells drawn by luminosity)
 //   tau_event = -ln R  Sec. 3.1.2, Eq. lnR
 //   cell march         Sec. 3.1.2 (tau_cell = (n sigma_0 H(a,x) + k_dust) l_cell,
 //                      x' = (x + k.u) sqrt(T/T') - k.u' at every face)
-//   scattering         Sec. 3.1.3 + 3.2.3 + 3.2.4 (device.cuh: scatter_hi)
+//   scattering         Sec. 3.1.3 + 3.2.3 + 3.2.4 (device.cuh: scatter_hi); a tau_0
+//                      for x_crit from the cell and non-local terms or from the
+//                      Jeans estimate (Eq. atau0J)
 //   peel-off           Sec. 6.1, Eq. SB (W(theta) exp(-tau_esc), stop at tau_esc > 50)
 //
 // GB300 design:
@@ -321,70 +325,100 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           const R st = m_sqrt(fmax(R(0), R(1) - mu * mu));
           k[0] = st * cp; k[1] = st * sp; k[2] = mu;
           tau.set(-m_log(b0.v[2]));
-          double r[3] = {P.src[0], P.src[1], P.src[2]};
-          if (P.src_sigma > 0.0) {
-            U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
-            const double rho1 = sqrt(-2.0 * log(b1.v[0])), rho2 = sqrt(-2.0 * log(b1.v[2]));
-            double s1, c1, s2, c2;
-            sincospi(2.0 * b1.v[1], &s1, &c1);
-            sincospi(2.0 * b1.v[3], &s2, &c2);
-            r[0] += P.src_sigma * rho1 * c1;
-            r[1] += P.src_sigma * rho1 * s1;
-            r[2] += P.src_sigma * rho2 * c2;
-          }
           bool inside = true;
-          if constexpr (kOct) {
-            // descend from the root, split planes lo + (2i + 1) h 2^-d
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              if (!(r[a] >= G.lo[a] && r[a] <= G.hi[a]) || (r[a] == G.lo[a] && k[a] < R(0)) ||
-                  (r[a] == G.hi[a] && !(k[a] < R(0))))
-                inside = false;
-              ci[a] = 0;
+          if (P.source == 1) {
+            // diffuse emission (Sec. 3.1.1): the cell is the first whose inclusive
+            // prefix weight exceeds t = floor(r w_tot 2^-64), r the 64-bit word of
+            // block 1; the position is uniform in the cell (block 3, words 0-2)
+            const u4 q1 = P.rng.block(rpid, 0, 1);
+            const unsigned long long t =
+                __umul64hi(((unsigned long long)q1.y << 32) | q1.x, G.lum_total);
+            int64_t lo = 0, hi = G.n_cells - 1;
+            while (lo < hi) {
+              const int64_t mid = (lo + hi) >> 1;
+              if (__ldg(G.lum_cum + mid) > t) hi = mid; else lo = mid + 1;
             }
-            lvl = 0;
-            if (inside) {
-              int32_t ch;
-              uint32_t v = 0;
-              while ((ch = __ldg(G.node + v)) >= 0 && lvl < kMaxOctLevel) {
-                ++lvl;
-                int cidx = 0;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                  // rounded product, then rounded sum (no fused multiply-add):
-                  // the same number as the leaf faces lying in this plane
-                  const double mid =
-                      __dadd_rn(G.lo[a], __dmul_rn((double)(2 * ci[a] + 1), G.h[a] * pow2neg<double>(lvl)));
-                  const int up = (r[a] > mid) || (r[a] == mid && !(k[a] < R(0)));
-                  ci[a] = 2 * ci[a] + up;
-                  cidx |= up << a;
-                }
-                v = (uint32_t)ch + (uint32_t)cidx;
-              }
-              leaf = -1 - (int64_t)__ldg(G.node + v);
-              if (leaf < 0 || leaf >= G.n_cells) { atomicExch(L.error, 1); inside = false; leaf = 0; }
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                const double hl = G.h[a] * pow2neg<double>(lvl);
-                xi[a].set_d((r[a] - __dadd_rn(G.lo[a], __dmul_rn((double)ci[a], hl))) / hl);
-              }
+            const U4<double> q3 = uniforms<double>(P.rng, rpid, 0, 3);
+            if constexpr (kOct) {
+              const uint32_t w0 = __ldg(G.leaf_loc + 3 * lo);
+              lvl = (int)(w0 >> 24);
+              ci[0] = (int)(w0 & 0xFFFFFFu);
+              ci[1] = (int)__ldg(G.leaf_loc + 3 * lo + 1);
+              ci[2] = (int)__ldg(G.leaf_loc + 3 * lo + 2);
+              leaf = lo;
+            } else {
+              const int64_t nxy = (int64_t)G.n[0] * G.n[1];
+              ci[2] = (int)(lo / nxy);
+              ci[1] = (int)((lo - ci[2] * nxy) / G.n[0]);
+              ci[0] = (int)(lo - ci[2] * nxy - (int64_t)ci[1] * G.n[0]);
             }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) xi[a].set_d(q3.v[a]);
           } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const double t = (r[a] - G.lo[a]) / G.h[a];
-              const double f = floor(t);
-              int i = 0;
-              double loc = 0.0;
-              const bool in_range = f >= -1.0 && f <= (double)G.n[a];
-              if (in_range) {
-                i = (int)f;
-                loc = t - f;
-                if (t == f && k[a] < R(0)) { i -= 1; loc = 1.0; }
+            double r[3] = {P.src[0], P.src[1], P.src[2]};
+            if (P.src_sigma > 0.0) {
+              U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
+              const double rho1 = sqrt(-2.0 * log(b1.v[0])), rho2 = sqrt(-2.0 * log(b1.v[2]));
+              double s1, c1, s2, c2;
+              sincospi(2.0 * b1.v[1], &s1, &c1);
+              sincospi(2.0 * b1.v[3], &s2, &c2);
+              r[0] += P.src_sigma * rho1 * c1;
+              r[1] += P.src_sigma * rho1 * s1;
+              r[2] += P.src_sigma * rho2 * c2;
+            }
+            if constexpr (kOct) {
+              // descend from the root, split planes lo + (2i + 1) h 2^-d
+  #pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                if (!(r[a] >= G.lo[a] && r[a] <= G.hi[a]) || (r[a] == G.lo[a] && k[a] < R(0)) ||
+                    (r[a] == G.hi[a] && !(k[a] < R(0))))
+                  inside = false;
+                ci[a] = 0;
               }
-              if (!in_range || i < 0 || i >= G.n[a]) { inside = false; i = 0; }
-              ci[a] = i;
-              xi[a].set_d(loc);
+              lvl = 0;
+              if (inside) {
+                int32_t ch;
+                uint32_t v = 0;
+                while ((ch = __ldg(G.node + v)) >= 0 && lvl < kMaxOctLevel) {
+                  ++lvl;
+                  int cidx = 0;
+  #pragma unroll
+                  for (int a = 0; a < 3; ++a) {
+                    // rounded product, then rounded sum (no fused multiply-add):
+                    // the same number as the leaf faces lying in this plane
+                    const double mid =
+                        __dadd_rn(G.lo[a], __dmul_rn((double)(2 * ci[a] + 1), G.h[a] * pow2neg<double>(lvl)));
+                    const int up = (r[a] > mid) || (r[a] == mid && !(k[a] < R(0)));
+                    ci[a] = 2 * ci[a] + up;
+                    cidx |= up << a;
+                  }
+                  v = (uint32_t)ch + (uint32_t)cidx;
+                }
+                leaf = -1 - (int64_t)__ldg(G.node + v);
+                if (leaf < 0 || leaf >= G.n_cells) { atomicExch(L.error, 1); inside = false; leaf = 0; }
+  #pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  const double hl = G.h[a] * pow2neg<double>(lvl);
+                  xi[a].set_d((r[a] - __dadd_rn(G.lo[a], __dmul_rn((double)ci[a], hl))) / hl);
+                }
+              }
+            } else {
+  #pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const double t = (r[a] - G.lo[a]) / G.h[a];
+                const double f = floor(t);
+                int i = 0;
+                double loc = 0.0;
+                const bool in_range = f >= -1.0 && f <= (double)G.n[a];
+                if (in_range) {
+                  i = (int)f;
+                  loc = t - f;
+                  if (t == f && k[a] < R(0)) { i -= 1; loc = 1.0; }
+                }
+                if (!in_range || i < 0 || i >= G.n[a]) { inside = false; i = 0; }
+                ci[a] = i;
+                xi[a].set_d(loc);
+              }
             }
           }
           x = R(0);
@@ -566,7 +600,10 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           }
         } else {
           R atau0 = R(-1);
-          if (P.core_skip) {
+          if (P.core_skip == 2) {
+            // Eq. atau0J: the Jeans estimate of the scattering cell
+            atau0 = prm<R>(P.jeans_c, P.jeans_cf) * m_sqrt(a * R(r0.x));
+          } else if (P.core_skip) {
             R lmin = R(3.0e38);
 #pragma unroll
             for (int q = 0; q < 3; ++q) lmin = fmin(lmin, fmin(xi[q].val(), xi[q].from_top()) * hh[q]);

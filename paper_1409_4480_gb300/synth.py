@@ -51,6 +51,7 @@ class Grid:
     leaf_level: Optional[np.ndarray] = None   # uint8  (octree)
     leaf_ijk: Optional[np.ndarray] = None     # uint32 (n_leaves, 3)
     meta: dict = dataclasses.field(default_factory=dict)
+    lum: Optional[np.ndarray] = None          # float64 per-cell luminosity (diffuse emission)
 
     @property
     def n_cells(self) -> int:
@@ -76,7 +77,7 @@ class RunSpec:
     seed: int
     src_pos: tuple = (0.0, 0.0, 0.0)
     src_sigma: float = 0.0
-    core_skip: bool = True
+    core_skip: int = 1              # 0 off, 1 a tau_cell + a tau_NL, 2 Jeans estimate
     recoil: bool = True
     phase: int = 0                  # 0 dipole/anisotropic, 1 isotropic
     f_nl: float = 0.5
@@ -97,6 +98,7 @@ class RunSpec:
     precision: int = 1              # 0 plain FP64, 1 mixed (FP32 transport)
     pid_offset: int = 0             # packets are ids pid_offset .. pid_offset + n_packets - 1
     emission: int = 0               # 0 line centre, 1 natural (Lorentzian) + thermal atom velocity
+    source: int = 0                 # 0 point (src_pos, src_sigma), 1 cells by luminosity (Grid.lum)
 
 
 def sigma0_recipe(T: float) -> float:
@@ -270,12 +272,32 @@ def octree_sphere(T: float, tau0: float, R: float = PC_CM, v_max_kms: float = 0.
 
 MSUN_G = 1.98847e33
 M_P_G = 1.67262192e-24
+E_LYA_ERG = 1.634e-11        # 10.2 eV
+
+
+def lya_luminosity(n_h, x_hi, T, volume):
+    """Per-cell Ly-alpha luminosity (erg/s) of gas with hydrogen density n_h
+    (cm^-3), neutral fraction x_hi and temperature T (K), in cells of the given
+    volume (cm^3): the two mechanisms of Sec. 3.1.1 for a hydrogen-only gas
+    with n_e = n_p = (1 - x_hi) n_h.
+      recombination: 0.68 E_Lya alpha_B n_e n_p, with the case-B coefficient
+        alpha_B ~ 2.5e-13 T4^-3/4 cm^3/s of Sec. 5.1 and the 0.68 Ly-alpha
+        photons per recombination of Sec. 5.3;
+      collisional excitation: 7.5e-19 erg cm^3/s (1 + T5^1/2)^-1 e^(-118348/T)
+        n_e n_HI (Sec. 5.3, after Cen 1992; the excited atoms are the neutral
+        ones, n_HI = x_hi n_h)."""
+    n_h, x_hi, T = (np.asarray(v, np.float64) for v in (n_h, x_hi, T))
+    n_e = (1.0 - x_hi) * n_h
+    alpha_b = 2.5e-13 * (T / 1e4) ** -0.75
+    rec = 0.68 * E_LYA_ERG * alpha_b * n_e * n_e
+    col = 7.5e-19 / (1.0 + np.sqrt(T / 1e5)) * np.exp(-118348.0 / T) * n_e * x_hi * n_h
+    return (rec + col) * np.asarray(volume, np.float64)
 
 
 def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, conc: float = 5.0,
          f_baryon: float = 0.157, x_h: float = 0.76, cone_half_angle_deg: float = 30.0,
          clump_sigma: float = 1.0, turb_kms: float = 10.0, min_level: int = 6, max_level: int = 12,
-         cone_level: int = 9, leaf_mass_frac: float = 3e-6) -> Grid:
+         cone_level: int = 9, leaf_mass_frac: float = 3e-6, emission: bool = False) -> Grid:
     """Synthetic first-galaxy halo on an octree (stand-in for the paper's AMR
     halo, whose simulation data are not available).
 
@@ -289,7 +311,10 @@ def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, c
     velocity of turb_kms per component per leaf.  No dust.
     Refinement: a node splits while its gas mass exceeds leaf_mass_frac of the
     gas mass inside r_vir (down to max_level), or while it straddles the cone
-    surface inside r_vir (down to cone_level), starting from min_level."""
+    surface inside r_vir (down to cone_level), starting from min_level.
+    emission: also set the per-leaf Ly-alpha luminosity of the gas
+    (lya_luminosity: recombination and collisional excitation), for diffuse
+    emission."""
     rng = np.random.default_rng(seed)
     R = 2.0 * r_vir
     lo, hi = np.array([-R] * 3), np.array([R] * 3)
@@ -328,6 +353,8 @@ def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, c
                   cone_half_angle_deg=cone_half_angle_deg, clump_sigma=clump_sigma, turb_kms=turb_kms,
                   min_level=min_level, max_level=max_level, cone_level=cone_level, leaf_mass_frac=leaf_mass_frac,
                   n_leaves=n)
+    if emission:
+        g.lum = lya_luminosity(n_h, x_hi, np.where(in_cone, 1e4, 100.0), s[:, 0] * s[:, 1] * s[:, 2])
     return g
 
 

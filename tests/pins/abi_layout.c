@@ -13,6 +13,7 @@ int main(void) {
   printf("off_scatter_n_trials %zu\n", offsetof(colt_scatter_io, n_trials));
   printf("off_run_precision %zu\n", offsetof(colt_run_params, precision));
   printf("off_run_emission %zu\n", offsetof(colt_run_params, emission));
+  printf("off_run_source %zu\n", offsetof(colt_run_params, source));
   printf("off_result_pk_freq %zu\n", offsetof(colt_result, pk_freq));
   return 0;
 }

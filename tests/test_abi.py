@@ -59,6 +59,7 @@ def test_binding_struct_layout_matches_header():
     assert sizes["off_scatter_n_trials"] == colt.ScatterIO.n_trials.offset
     assert sizes["off_run_precision"] == colt.RunParams.precision.offset
     assert sizes["off_run_emission"] == colt.RunParams.emission.offset
+    assert sizes["off_run_source"] == colt.RunParams.source.offset
     assert sizes["off_result_pk_freq"] == colt.Result.pk_freq.offset
 
 
