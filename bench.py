@@ -480,6 +480,69 @@ def run_octree(args):
     C.colt_finalize(ctx)
 
 
+def slab_suite():
+    """The temperature suites of uniform slabs (App. "Thermal effects"): tau0 = 1e7
+    at T = 10, 1e2, 1e3, 1e4, 1e5 K, and a fixed column N_H = 1.7e20 cm^-2
+    (tau0 = 1e7 T4^-1/2) at T = 10, 1e2, 1e3, 1e4 K; 64^3 periodic slabs, recoil on,
+    angle-averaged spectra over +-300 km/s."""
+    out = [("tau0", T, 1e7) for T in (10.0, 1e2, 1e3, 1e4, 1e5)]
+    out += [("column", T, 1e7 * (T / 1e4) ** -0.5) for T in (10.0, 1e2, 1e3, 1e4)]
+    return out
+
+
+def run_slab_suite(args):
+    """Served steps of the nine temperature-suite slabs (same timing rules)."""
+    import torch
+    from paper_1409_4480_gb300 import colt as C
+    world, rank, local = _rank_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = C.colt_init(local, 0, stream.cuda_stream)
+    suite = slab_suite()
+    hs = [C.colt_create_grid(ctx, S.slab(64, T, tau0)) for _, T, tau0 in suite]
+    B = args.packets_per_case
+
+    def specs_of(s):
+        off = (s * world + rank) * B
+        return [S.RunSpec(n_packets=B, seed=500 + i, T_ref=T, spec_units=1, spec_lo=-300.0, spec_hi=300.0,
+                          spec_nbins=120, precision=1, pid_offset=off) for i, (_, T, _) in enumerate(suite)]
+
+    def run_steps(s0, n):
+        rids = [(C.colt_submit(ctx, hs[i], sp), sp) for s in range(s0, s0 + n) for i, sp in enumerate(specs_of(s))]
+        res = []
+        for rid, sp in rids:
+            C.colt_wait(ctx, rid, -1.0)
+        for rid, sp in rids:
+            res.append((C.colt_poll(ctx, rid), C.colt_read_result(ctx, rid, sp)))
+            C.colt_release(ctx, rid)
+        return res
+
+    run_steps(0, args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        done = run_steps(args.warmup, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    scat = sum(r["n_scat"] for _, r in done)
+    pk = sum(r["n_emitted"] for _, r in done)
+    lat = sorted(st["latency_ms"] for st, _ in done)
+    line = {"metric": METRIC, "value": scat / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "photons_per_s": pk / (ms / 1e3),
+            "served_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                  "n_requests": len(lat)},
+            "config": {"workload": "slab64_temperature_suites_9", "cases": [f"{k} T={T:g} tau0={t:.3g}"
+                                                                           for k, T, t in suite],
+                       "packets_per_case_per_step": B, "precision": "mixed", "recoil": True},
+            "counts": {"scatterings": scat, "packets": pk}, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    C.colt_finalize(ctx)
+
+
 def serving_requests(n):
     """The serving mix: request i (seed 4000 + i) is a sphere or a slab on a
     64^3 grid with tau0 log-uniform in [1e4, 1e8], T log-uniform in [10, 1e5] K,
@@ -598,7 +661,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="colt", choices=["colt", "reference"])
     ap.add_argument("--workload", default="sphere128",
-                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving"])
+                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving", "tslab"])
     ap.add_argument("--core-skip", type=int, default=1, choices=[0, 1, 2],
                     help="octree workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
     ap.add_argument("--requests", type=int, default=256)
@@ -624,6 +687,8 @@ def main():
         run_octree(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "tslab":
+        run_slab_suite(args)
     else:
         run_gpu(args)
 
