@@ -543,6 +543,92 @@ def run_slab_suite(args):
     C.colt_finalize(ctx)
 
 
+GALAXY_MODELS = [(m, M) for M in (1e5, 1e6, 1e7, 1e8) for m in ("SE", "SL", "WE", "WL")]
+
+
+def galaxy_observables(res):
+    """Table-3 quantities of one solve: F/F_Omega face-on (+-z cameras) and
+    edge-on (+-x, +-y), and the red/blue flux ratios F_r/F_b (Delta v > 0 vs
+    < 0) along z, xy and angle-averaged (the escape spectrum)."""
+    cs = np.asarray(res["cam_spec"], np.float64)           # cameras: +x -x +y -y +z -z
+    ct = cs.sum(axis=1)
+    esc = max(float(np.sum(res["spec"])), 1.0)               # the same (wide) velocity range
+    h = cs.shape[1] // 2
+    rb = lambda s: float(s[h:].sum() / max(s[:h].sum(), 1e-300))
+    sp = np.asarray(res["spec"], np.float64)
+    return {"F/F_Omega_z": float(ct[4:6].mean() / esc), "F/F_Omega_xy": float(ct[0:4].mean() / esc),
+            "Fr/Fb_z": rb(cs[4:6].sum(axis=0)), "Fr/Fb_xy": rb(cs[0:4].sum(axis=0)),
+            "Fr/Fb_Omega": float(sp[len(sp) // 2:].sum() / max(sp[:len(sp) // 2].sum(), 1)),
+            "f_esc": res["n_escaped"] / max(res["n_emitted"], 1)}
+
+
+def run_galaxies(args):
+    """Served steps over the 16 idealized first-galaxy models (Sec. 5.1:
+    SE/SL/WE/WL x M_H,tot = 1e5..1e8 Msun), with their Table-3 observables."""
+    import torch
+    from paper_1409_4480_gb300 import colt as C
+    world, rank, local = _rank_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = C.colt_init(local, 0, stream.cuda_stream)
+    grids = [S.galaxy(m, M) for m, M in GALAXY_MODELS]
+    hs = [C.colt_create_grid(ctx, g) for g in grids]
+    B = args.packets_per_case
+    cams = S.axis_cameras(0)
+
+    def specs_of(s):
+        off = (s * world + rank) * B
+        return [S.RunSpec(n_packets=B, seed=600 + i, recoil=True, albedo=0.0, core_skip=args.core_skip,
+                          spec_units=1, spec_lo=-3000.0,
+                          spec_hi=3000.0, spec_nbins=300, cameras=cams, cam_units=1, cam_lo=-3000.0,
+                          cam_hi=3000.0, cam_nbins=300, precision=1, pid_offset=off)
+                for i in range(len(hs))]
+
+    def run_steps(s0, n):
+        rids = [(i, C.colt_submit(ctx, hs[i], sp), sp) for s in range(s0, s0 + n)
+                for i, sp in enumerate(specs_of(s))]
+        res = []
+        for i, rid, sp in rids:
+            C.colt_wait(ctx, rid, -1.0)
+        for i, rid, sp in rids:
+            res.append((i, C.colt_poll(ctx, rid), C.colt_read_result(ctx, rid, sp)))
+            C.colt_release(ctx, rid)
+        return res
+
+    run_steps(0, args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        done = run_steps(args.warmup, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    scat = sum(r["n_scat"] for _, _, r in done)
+    pk = sum(r["n_emitted"] for _, _, r in done)
+    lat = sorted(st["latency_ms"] for _, st, _ in done)
+    # observables per model, summed over the timed steps
+    obs = {}
+    for i, (m, M) in enumerate(GALAXY_MODELS):
+        rs = [r for j, _, r in done if j == i]
+        tot = {k: (np.sum([r[k] for r in rs], axis=0) if k in ("cam_spec", "spec")
+                   else sum(r[k] for r in rs)) for k in ("cam_spec", "spec", "n_escaped", "n_emitted")}
+        obs[f"{m}{int(round(np.log10(M)))}"] = {k: round(v, 3) for k, v in galaxy_observables(tot).items()}
+    line = {"metric": METRIC, "value": scat / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "photons_per_s": pk / (ms / 1e3),
+            "served_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                  "n_requests": len(lat)},
+            "config": {"workload": "idealized_galaxies_16", "models": "SE/SL/WE/WL x M_H,tot 1e5-1e8 Msun",
+                       "core_skip": ["off", "cell + non-local a tau", "Jeans a tau"][args.core_skip],
+                       "leaves": [int(g.n_cells) for g in grids], "packets_per_model_per_step": B,
+                       "precision": "mixed"},
+            "counts": {"scatterings": scat, "packets": pk}, "clocks": clk.summary(), "observables": obs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    C.colt_finalize(ctx)
+
+
 def serving_requests(n):
     """The serving mix: request i (seed 4000 + i) is a sphere or a slab on a
     64^3 grid with tau0 log-uniform in [1e4, 1e8], T log-uniform in [10, 1e5] K,
@@ -661,9 +747,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="colt", choices=["colt", "reference"])
     ap.add_argument("--workload", default="sphere128",
-                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving", "tslab"])
+                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving", "tslab", "galaxies"])
     ap.add_argument("--core-skip", type=int, default=1, choices=[0, 1, 2],
-                    help="octree workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
+                    help="octree and galaxy workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.75)
     ap.add_argument("--packets-per-case", type=int, default=125000)
@@ -689,6 +775,8 @@ def main():
         run_serving(args)
     elif args.workload == "tslab":
         run_slab_suite(args)
+    elif args.workload == "galaxies":
+        run_galaxies(args)
     else:
         run_gpu(args)
 

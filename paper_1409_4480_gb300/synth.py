@@ -358,6 +358,127 @@ def halo(seed: int = 3, r_vir: float = 600.0 * PC_CM, m_vir_msun: float = 1e8, c
     return g
 
 
+# ------------------------------------------------ idealized first galaxies --
+# Sec. 5.1: cored isothermal hydrogen profile inside a neutral IGM, an early
+# (Stromgren sphere) or late (plus a bicone) ionized region, static or
+# radiation-driven wind, T = 1e4 K, on an octree refined by the Jeans, Sobolev
+# and geometric criteria.  Planck 2013 parameters as Sec. 5.1 prints them.
+H0_KMS_MPC, OMEGA_B, X_HYDROGEN = 67.8, 0.0485, 0.75
+G_CGS = 6.67430e-8
+M_H_G = 1.6735575e-24          # hydrogen atom
+MPC_CM = 1e6 * PC_CM
+K_B_CGS = 1.380649e-16
+
+
+def n_h_igm(z: float) -> float:
+    """Background hydrogen density rho_cr,0 X Omega_b (1 + z)^3 / m_H (cm^-3)."""
+    h0 = H0_KMS_MPC * 1e5 / MPC_CM
+    rho_cr0 = 3.0 * h0 * h0 / (8.0 * math.pi * G_CGS)
+    return rho_cr0 * X_HYDROGEN * OMEGA_B * (1.0 + z) ** 3 / M_H_G
+
+
+def galaxy_chi(m_h_tot_msun: float, r_core: float, z: float) -> float:
+    """chi = n_IGM^(-1/3) / r_core (M_H,tot / (4 pi m_H))^(1/3) (Eq. chi)."""
+    return n_h_igm(z) ** (-1.0 / 3.0) / r_core * (m_h_tot_msun * MSUN_G / (4.0 * math.pi * M_H_G)) ** (1.0 / 3.0)
+
+
+def galaxy_core_density(m_h_tot_msun: float, r_core: float, z: float) -> float:
+    """n_H,0 normalising the profile to M_H,tot exactly: with y = (n_0/n_IGM)^1/2,
+    Eq. MHtot reads y^3 - (2/3) y^2 = chi^3 (solved by Newton's method from y = chi)."""
+    c3 = galaxy_chi(m_h_tot_msun, r_core, z) ** 3
+    y = max(1.0, c3 ** (1.0 / 3.0))
+    for _ in range(100):
+        f = y ** 3 - (2.0 / 3.0) * y * y - c3
+        y_new = y - f / (3.0 * y * y - (4.0 / 3.0) * y)
+        if abs(y_new - y) <= 1e-15 * y:
+            y = y_new
+            break
+        y = y_new
+    return n_h_igm(z) * y * y
+
+
+def jeans_length(T, n_h):
+    """lambda_J = sqrt(15 k T / (4 pi G mu rho)), mu = 1.23 m_H, rho = m_H n_H / X (Sec. 3.2.4)."""
+    rho = M_H_G * np.asarray(n_h, np.float64) / X_HYDROGEN
+    return np.sqrt(15.0 * K_B_CGS * np.asarray(T, np.float64) / (4.0 * math.pi * G_CGS * 1.23 * M_H_G * rho))
+
+
+def galaxy(model: str, m_h_tot_msun: float, z: float = 10.0, r_core: float = 10.0 * PC_CM,
+           T: float = 1e4, v_inf_kms: float = 10.0, r_star: float = PC_CM, cone_half_angle_deg: float = 30.0,
+           n_jeans: int = 64, n_sobolev: int = 32, n_geo: int = 64, n_cone: int = 512,
+           min_level: int = 4, max_level: int = 20) -> Grid:
+    """Idealized first galaxy of Sec. 5.1 on an octree; model is one of "SE",
+    "SL", "WE", "WL" (Static / Wind, Early / Late).
+
+    n_H: n_H,0 for r <= r_core, n_H,0 (r / r_core)^-2 out to r_edge =
+    r_core (n_H,0 / n_IGM)^1/2, n_IGM beyond (Eq. nHprofile), with n_H,0 from
+    M_H,tot (Eq. MHtot).  Early: no neutral hydrogen inside the Stromgren
+    sphere R_S = r_core; Late: also none inside the bicone of half-angle 30 deg
+    about z out to r_edge.  Wind: v = v_inf (1 - R_*/r)^1/2 radially (Eq. wind)
+    beyond R_*.  T uniform.  Box (-2 r_edge, 2 r_edge)^3.  Refinement
+    (Sec. 5.1.4): split a node while its size exceeds lambda_J / n_jeans at its
+    centre density, or (wind) the Sobolev length v_th / |dv/dr| / n_sobolev, or
+    while it holds a point of the sphere r = r_edge or r = r_core and is larger
+    than that radius / n_geo, or (late) while it straddles the cone surface
+    inside r_edge and is larger than r_edge / n_cone.  Fields at leaf centres.
+    The models are built at z = 10 (Sec. 5.1: "at redshift z ~ 10"; this
+    reproduces the printed edge radii 1.09, 2.35, 5.05 and 10.88 kpc of the
+    5- to 8-models) and observed at z = 9 (the flux tables).  The Sobolev
+    criterion applies only outside the Stromgren sphere, where gas can be
+    neutral (at R_* the wind's gradient diverges)."""
+    if model not in ("SE", "SL", "WE", "WL"):
+        raise ValueError("model must be SE, SL, WE or WL")
+    wind, late = model[0] == "W", model[1] == "L"
+    n_igm = n_h_igm(z)
+    n0 = galaxy_core_density(m_h_tot_msun, r_core, z)
+    r_edge = r_core * math.sqrt(n0 / n_igm)
+    R = 2.0 * r_edge
+    lo, hi = np.array([-R] * 3), np.array([R] * 3)
+    cos_c, sin_c = math.cos(math.radians(cone_half_angle_deg)), math.sin(math.radians(cone_half_angle_deg))
+    vth = 12.85e5 * math.sqrt(T / 1e4)          # cm/s (Sec. 2)
+
+    def n_of(r):
+        return np.where(r <= r_core, n0, np.where(r < r_edge, n0 * (r_core / np.maximum(r, r_core)) ** 2, n_igm))
+
+    def refine(c, s, L):
+        r = np.linalg.norm(c, axis=1)
+        h = s[:, 0]
+        half_diag = 0.5 * np.linalg.norm(s, axis=1)
+        out = h * n_jeans > jeans_length(T, n_of(r))
+        if wind:
+            # only where the gas can be neutral (outside the Stromgren sphere)
+            rr = np.maximum(r, r_star * (1.0 + 1e-9))
+            dvdr = v_inf_kms * 1e5 * 0.5 / np.sqrt(1.0 - r_star / rr) * r_star / rr ** 2
+            out |= (r + half_diag > r_core) & (h * n_sobolev * dvdr > vth)
+        for rx in (r_edge, r_core):
+            out |= (np.abs(r - rx) < half_diag) & (h * n_geo > rx)
+        if late:
+            dist = np.abs(np.abs(c[:, 2]) * sin_c - np.hypot(c[:, 0], c[:, 1]) * cos_c)
+            out |= (dist < half_diag) & (r < r_edge + half_diag) & (h * n_cone > r_edge)
+        return out
+
+    lv, ijk = octree_refine(lo, hi, refine, min_level, max_level)
+    c, s = leaf_geometry(lo, hi, lv, ijk)
+    r = np.linalg.norm(c, axis=1)
+    n_h = n_of(r)
+    ionized = r < r_core                                  # Stromgren sphere, R_S = r_core
+    if late:
+        ionized |= (np.abs(c[:, 2]) > cos_c * r) & (r < r_edge)
+    n_hi = np.where(ionized, 0.0, n_h)
+    fields = dict(n_HI=n_hi, T=np.full(len(lv), T))
+    if wind:
+        rs = np.maximum(r, 1e-300)
+        v = np.where(r > r_star, v_inf_kms * np.sqrt(np.clip(1.0 - r_star / rs, 0.0, None)), 0.0)
+        for a, k in enumerate(("vx", "vy", "vz")):
+            fields[k] = v * c[:, a] / rs
+    g = octree_grid(lo, hi, lv, ijk, fields)
+    g.meta = dict(model=f"{model}{int(round(math.log10(m_h_tot_msun)))}", m_h_tot_msun=m_h_tot_msun, z=z,
+                  r_core=r_core, r_edge=r_edge, n_h0=n0, n_h_igm=n_igm, T=T, v_inf_kms=v_inf_kms, r_star=r_star,
+                  cone_half_angle_deg=cone_half_angle_deg, n_jeans=n_jeans, n_sobolev=n_sobolev, n_geo=n_geo,
+                  n_cone=n_cone, n_leaves=len(lv), levels=(int(lv.min()), int(lv.max())))
+    return g
+
+
 def _trilinear(field: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Periodic trilinear interpolation of field[z, y, x] at fractional grid
     coordinates u (m, 3) = (x, y, z) in units of the grid spacing (cell centres
