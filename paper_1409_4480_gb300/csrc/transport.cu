@@ -120,6 +120,47 @@ __device__ __forceinline__ int64_t cell_index(const GridDev& G, const int c3[3])
   return (int64_t)c3[0] + G.stride[1] * c3[1] + G.stride[2] * c3[2];
 }
 
+// Diffuse emission (Sec. 3.1.1): the cell is the first whose inclusive prefix
+// weight exceeds t = floor(r w_tot 2^-64), r the 64-bit word of event-0 block 1;
+// the position is uniform in the cell (event-0 block 3, words 0-2).  Runs once
+// per packet: kept out of line so that the transport loop's code stays compact.
+struct EmitCell {
+  int64_t cell;
+  int ci[3];
+  int lvl;
+  double f[3];
+};
+
+__device__ __noinline__ EmitCell pick_emission_cell(const GridDev& G, const Rng& rng, uint64_t rpid) {
+  EmitCell out;
+  const u4 q1 = rng.block(rpid, 0, 1);
+  const unsigned long long t = __umul64hi(((unsigned long long)q1.y << 32) | q1.x, G.lum_total);
+  int64_t lo = 0, hi = G.n_cells - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(G.lum_cum + mid) > t) hi = mid; else lo = mid + 1;
+  }
+  out.cell = lo;
+  if (G.kind == 1) {
+    const uint32_t w0 = __ldg(G.leaf_loc + 3 * lo);
+    out.lvl = (int)(w0 >> 24);
+    out.ci[0] = (int)(w0 & 0xFFFFFFu);
+    out.ci[1] = (int)__ldg(G.leaf_loc + 3 * lo + 1);
+    out.ci[2] = (int)__ldg(G.leaf_loc + 3 * lo + 2);
+  } else {
+    const int64_t nxy = (int64_t)G.n[0] * G.n[1];
+    out.lvl = 0;
+    out.ci[2] = (int)(lo / nxy);
+    out.ci[1] = (int)((lo - out.ci[2] * nxy) / G.n[0]);
+    out.ci[0] = (int)(lo - out.ci[2] * nxy - (int64_t)out.ci[1] * G.n[0]);
+  }
+  const U4<double> q3 = uniforms<double>(rng, rpid, 0, 3);
+  out.f[0] = q3.v[0];
+  out.f[1] = q3.v[1];
+  out.f[2] = q3.v[2];
+  return out;
+}
+
 // kMinBlocks: resident CTAs per SM the register allocation must allow (1: the
 // compiler's choice; 3: at most 85 registers; 4: at most 64)
 template <typename R, int kWarps, bool kOct, int kMinBlocks>
@@ -327,33 +368,16 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           tau.set(-m_log(b0.v[2]));
           bool inside = true;
           if (P.source == 1) {
-            // diffuse emission (Sec. 3.1.1): the cell is the first whose inclusive
-            // prefix weight exceeds t = floor(r w_tot 2^-64), r the 64-bit word of
-            // block 1; the position is uniform in the cell (block 3, words 0-2)
-            const u4 q1 = P.rng.block(rpid, 0, 1);
-            const unsigned long long t =
-                __umul64hi(((unsigned long long)q1.y << 32) | q1.x, G.lum_total);
-            int64_t lo = 0, hi = G.n_cells - 1;
-            while (lo < hi) {
-              const int64_t mid = (lo + hi) >> 1;
-              if (__ldg(G.lum_cum + mid) > t) hi = mid; else lo = mid + 1;
-            }
-            const U4<double> q3 = uniforms<double>(P.rng, rpid, 0, 3);
-            if constexpr (kOct) {
-              const uint32_t w0 = __ldg(G.leaf_loc + 3 * lo);
-              lvl = (int)(w0 >> 24);
-              ci[0] = (int)(w0 & 0xFFFFFFu);
-              ci[1] = (int)__ldg(G.leaf_loc + 3 * lo + 1);
-              ci[2] = (int)__ldg(G.leaf_loc + 3 * lo + 2);
-              leaf = lo;
-            } else {
-              const int64_t nxy = (int64_t)G.n[0] * G.n[1];
-              ci[2] = (int)(lo / nxy);
-              ci[1] = (int)((lo - ci[2] * nxy) / G.n[0]);
-              ci[0] = (int)(lo - ci[2] * nxy - (int64_t)ci[1] * G.n[0]);
-            }
+            const EmitCell ec = pick_emission_cell(G, P.rng, rpid);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) xi[a].set_d(q3.v[a]);
+            for (int a = 0; a < 3; ++a) {
+              ci[a] = ec.ci[a];
+              xi[a].set_d(ec.f[a]);
+            }
+            if constexpr (kOct) {
+              lvl = ec.lvl;
+              leaf = ec.cell;
+            }
           } else {
             double r[3] = {P.src[0], P.src[1], P.src[2]};
             if (P.src_sigma > 0.0) {
