@@ -357,7 +357,7 @@ int ensure_slot(colt_ctx* ctx, int si) {
 // Enqueue one persistent launch over the jobs staged in the slot's host
 // buffer: header/job-table copy, counter reset, kernel.  Recorded once per
 // (slot, precision) as a CUDA graph and replayed.
-int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_per_sm) {
+int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_per_sm, bool extras) {
   Slot& sl = ctx->slots[si];
   LaunchBuf& lb = sl.lb;
   const int gi = precision == COLT_PLAIN ? 0 : 1;
@@ -368,12 +368,12 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
     CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
     CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant, blocks_per_sm,
-                        ctx->sm_count, sl.stream));
+                        ctx->sm_count, sl.stream, extras));
     CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
   }
-  const int code = cfg.variant * 64 + cfg.blocks_per_sm;
+  const int code = cfg.variant * 64 + cfg.blocks_per_sm + (extras ? 4096 : 0);
   if (sl.graph[gi][gk] && sl.graph_cfg[gi][gk] != code) {
     cudaGraphExecDestroy(sl.graph[gi][gk]);
     sl.graph[gi][gk] = nullptr;
@@ -384,7 +384,7 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
     cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
     cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant,
-                                      cfg.blocks_per_sm, ctx->sm_count, sl.stream);
+                                      cfg.blocks_per_sm, ctx->sm_count, sl.stream, extras);
     cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                     cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
@@ -747,6 +747,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   uint64_t left = kStepPackets;
   unsigned long long total = 0;
   int nj = 0;
+  bool extras = false;
   sl.jobs.clear();
   for (size_t i = 0; i < sel.size() && left > 0; ++i) {
     Req* r = sel[i];
@@ -760,6 +761,7 @@ int serve_launch(colt_ctx* ctx, int si) {
     J.p = r->run;
     J.p.n_packets = take;
     J.p.pid_offset = r->run.pid_offset + r->next_local;
+    extras = extras || run_needs_extras(J.p);
     total += take;
     lb.end_h()[nj] = total;
     r->next_local += take;
@@ -778,7 +780,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   h->total = total;
   // tallies were allocated and zeroed on the context stream
   CU(cudaStreamWaitEvent(sl.stream, ctx->ev_alloc, 0));
-  rc = enqueue_launch(ctx, si, prec, kind, 0);
+  rc = enqueue_launch(ctx, si, prec, kind, 0, extras);
   if (rc) return rc;
   CU(cudaLaunchHostFunc(sl.stream, slot_done_cb, ctx));
   CU(cudaEventRecord(sl.done, sl.stream));
@@ -1048,6 +1050,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   for (int i = 0; i < n; ++i) ord[i] = i;
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return grid_cost(*gs[a]) > grid_cost(*gs[b]); });
   unsigned long long total = 0;
+  bool extras = false;
   for (int q = 0; q < n; ++q) {
     const int i = ord[q];
     rc = alloc_tally(ctx, &params[i], per_packet[i], &ts[i]);
@@ -1055,6 +1058,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     Job& J = lb.jobs_h()[q];
     J.g = gs[i]->dev;
     J.p = make_run(*gs[i], &params[i]);
+    extras = extras || run_needs_extras(J.p);
     attach_tally(&J.p, ts[i]);
     total += params[i].n_packets;
     lb.end_h()[q] = total;
@@ -1066,7 +1070,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   float ms = 0;
   if (total > 0) {
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
-    rc = enqueue_launch(ctx, 0, prec, kind, params[0].blocks_per_sm);
+    rc = enqueue_launch(ctx, 0, prec, kind, params[0].blocks_per_sm, extras);
     if (rc) { free_all(); return rc; }
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     CU(cudaMemcpyAsync(lcnt, lb.work + 1, sizeof(lcnt), cudaMemcpyDeviceToHost, ctx->stream));

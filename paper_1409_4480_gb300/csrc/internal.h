@@ -170,9 +170,13 @@ struct LaunchDev {
 // All jobs of a launch share one grid kind (COLT_CARTESIAN / COLT_OCTREE).
 // variant: 0 = the compiler's register allocation, 1 / 2 = registers capped
 // for four / three CTAs per SM (FP32 only; transport_variants gives the count);
-// blocks_per_sm 0 = as many CTAs as fit.
+// blocks_per_sm 0 = as many CTAs as fit.  extras: some job uses diffuse
+// emission or the Jeans core-skipping estimate (their kernel instantiation,
+// register variant 0).
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
-                             int sm_count, cudaStream_t s);
+                             int sm_count, cudaStream_t s, bool extras);
+// true when a job needs the extras instantiation
+inline bool run_needs_extras(const RunDev& r) { return r.source == 1 || r.core_skip == 2; }
 int transport_variants(int precision);
 // resident CTAs per SM of a variant
 int transport_occupancy(int precision, int kind, int variant);

@@ -88,6 +88,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
   Job* jobs = reinterpret_cast<Job*>(host + kOffJobs);
   const int precision = params[0].precision;
   unsigned long long total = 0;
+  bool extras = false;
   for (int i = 0; i < n; ++i) {
     const colt_grid_view& gv = grids[i];
     const colt_run_params& p = params[i];
@@ -133,6 +134,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     r.recoil = p.recoil ? 1 : 0;
     r.phase = p.phase;
     r.emission = p.emission;
+    extras = extras || run_needs_extras(r);
     r.tau_max = p.tau_esc_max;
     r.albedo = p.albedo;
     r.max_scatter = p.max_scatter;
@@ -201,7 +203,7 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
   if (cudaMemcpyAsync(scratch, host, kOffJobs + sizeof(Job) * n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return COLT_ECUDA;
   if (total > 0 && launch_transport(reinterpret_cast<const LaunchDev*>(scratch), precision, COLT_CARTESIAN, 0,
-                                    params[0].blocks_per_sm, sm_count, stream) != cudaSuccess)
+                                    params[0].blocks_per_sm, sm_count, stream, extras) != cudaSuccess)
     return COLT_ECUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return COLT_ECUDA;
   int flag = 0;

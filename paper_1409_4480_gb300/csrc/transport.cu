@@ -163,7 +163,10 @@ __device__ __noinline__ EmitCell pick_emission_cell(const GridDev& G, const Rng&
 
 // kMinBlocks: resident CTAs per SM the register allocation must allow (1: the
 // compiler's choice; 3: at most 85 registers; 4: at most 64)
-template <typename R, int kWarps, bool kOct, int kMinBlocks>
+// kX: the instantiation that also holds diffuse emission and the Jeans
+// core-skipping estimate (launched only when a job of the launch uses them;
+// the common instantiation leaves their code out of the loop entirely).
+template <typename R, int kWarps, bool kOct, int kMinBlocks, bool kX>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
 k_transport(const LaunchDev* __restrict__ Lp) {
   const LaunchDev L = *Lp;
@@ -367,7 +370,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           k[0] = st * cp; k[1] = st * sp; k[2] = mu;
           tau.set(-m_log(b0.v[2]));
           bool inside = true;
-          if (P.source == 1) {
+          if (kX && P.source == 1) {
             const EmitCell ec = pick_emission_cell(G, P.rng, rpid);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -624,7 +627,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
           }
         } else {
           R atau0 = R(-1);
-          if (P.core_skip == 2) {
+          if (kX && P.core_skip == 2) {
             // Eq. atau0J: the Jeans estimate of the scattering cell
             atau0 = prm<R>(P.jeans_c, P.jeans_cf) * m_sqrt(a * R(r0.x));
           } else if (P.core_skip) {
@@ -859,11 +862,11 @@ constexpr size_t transport_smem() {
   return (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * 8;
 }
 
-template <typename R, bool kOct, int kMinBlocks>
+template <typename R, bool kOct, int kMinBlocks, bool kX = false>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
   constexpr int kWarps = 8;
   const size_t smem = transport_smem<R>();
-  auto kern = k_transport<R, kWarps, kOct, kMinBlocks>;
+  auto kern = k_transport<R, kWarps, kOct, kMinBlocks, kX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -878,7 +881,7 @@ static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStrea
 template <typename R, bool kOct, int kMinBlocks>
 static int occupancy_t() {
   constexpr int kWarps = 8;
-  auto kern = k_transport<R, kWarps, kOct, kMinBlocks>;
+  auto kern = k_transport<R, kWarps, kOct, kMinBlocks, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem<R>()) != cudaSuccess)
     return 1;
   int occ = 0;
@@ -889,7 +892,15 @@ static int occupancy_t() {
 int transport_variants(int precision) { return precision == 0 ? 1 : 3; }
 
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
-                             int sm_count, cudaStream_t s) {
+                             int sm_count, cudaStream_t s, bool extras) {
+  if (extras) {
+    // diffuse emission / Jeans estimate: the compiler's register allocation
+    if (precision == 0)
+      return kind == 1 ? launch_t<double, true, 1, true>(L, blocks_per_sm, sm_count, s)
+                       : launch_t<double, false, 1, true>(L, blocks_per_sm, sm_count, s);
+    return kind == 1 ? launch_t<float, true, 1, true>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<float, false, 1, true>(L, blocks_per_sm, sm_count, s);
+  }
   if (precision == 0) {
     return kind == 1 ? launch_t<double, true, 1>(L, blocks_per_sm, sm_count, s)
                      : launch_t<double, false, 1>(L, blocks_per_sm, sm_count, s);
