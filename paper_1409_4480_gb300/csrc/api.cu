@@ -985,24 +985,31 @@ int colt_set_cell_luminosity(colt_ctx* ctx, colt_grid grid, const double* lum, i
       loc[3 * c + 2] = g.leaf_ijk[3 * c + 2];
     }
   }
-  cudaStreamSynchronize(ctx->stream);
+  // the new table is complete on the device before the old one is released,
+  // so a failure leaves the grid as it was
+  unsigned long long* cum_d = nullptr;
+  uint32_t* loc_d = nullptr;
+  auto release_new = [&]() {
+    if (cum_d) cudaFree(cum_d);
+    if (loc_d) cudaFree(loc_d);
+  };
+  cudaError_t e = cudaMalloc(&cum_d, sizeof(unsigned long long) * (size_t)n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cum_d, cum.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && oct) e = cudaMalloc(&loc_d, sizeof(uint32_t) * 3 * (size_t)n);
+  if (e == cudaSuccess && oct)
+    e = cudaMemcpyAsync(loc_d, loc.data(), sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    release_new();
+    return cuda_fail(ctx, e, "luminosity table");
+  }
   if (g.lum_cum) cudaFree(g.lum_cum);
   if (g.leaf_loc) cudaFree(g.leaf_loc);
-  g.lum_cum = nullptr;
-  g.leaf_loc = nullptr;
-  g.dev.lum_cum = nullptr;
-  g.dev.leaf_loc = nullptr;
-  g.dev.lum_total = 0;
   ctx->used -= g.lum_bytes;
   g.bytes -= g.lum_bytes;
-  g.lum_bytes = 0;
-  CU(cudaMalloc(&g.lum_cum, sizeof(unsigned long long) * (size_t)n));
-  CU(cudaMemcpyAsync(g.lum_cum, cum.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
-  if (oct) {
-    CU(cudaMalloc(&g.leaf_loc, sizeof(uint32_t) * 3 * (size_t)n));
-    CU(cudaMemcpyAsync(g.leaf_loc, loc.data(), sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
-  }
-  CU(cudaStreamSynchronize(ctx->stream));
+  g.lum_cum = cum_d;
+  g.leaf_loc = loc_d;
   g.dev.lum_cum = g.lum_cum;
   g.dev.leaf_loc = g.leaf_loc;
   g.dev.lum_total = acc;
