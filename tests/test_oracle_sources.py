@@ -176,3 +176,32 @@ def test_jeans_core_skip_keeps_the_spectrum(O):
     chi2 = np.sum((a[m] - b[m]) ** 2 / (a[m] + b[m]))
     assert stats.chi2.sf(chi2, np.count_nonzero(m) - 1) > 1e-3
     assert runs[1]["n_scat"] < runs[0]["n_scat"]
+
+
+def test_diffuse_natural_emission_mixes_the_cells_voigt_profiles(O):
+    # diffuse natural + thermal emission from an empty box of two cells at
+    # 100 K and 1e4 K with luminosities 1 : 3: every packet leaves unscattered
+    # with the frequency it was born with, so the escape spectrum in Delta v is
+    # the luminosity-weighted mix of the two cells' Voigt profiles, each
+    # H(a,x)/sqrt(pi) in x = -Delta v / v_th (exact H from the Faddeeva function)
+    from scipy.special import wofz
+    g = S.uniform_box((2, 1, 1), (-1e18,) * 3, (1e18,) * 3, 1e-30, 1e4)
+    g.T = np.array([100.0, 1e4], np.float32)
+    g.lum = np.array([1.0, 3.0])
+    N = 80000
+    edges = np.linspace(-60.0, 60.0, 61)
+    spec = S.RunSpec(n_packets=N, seed=75, source=1, emission=1, spec_units=1, spec_lo=-60.0, spec_hi=60.0,
+                     spec_nbins=60)
+    r = O.run(g, spec)
+    assert r["n_escaped"] == N and r["n_scat"] == 0
+    v = np.linspace(-60.0, 60.0, 60 * 200 + 1)
+    p = np.zeros_like(v)
+    for T, w in ((100.0, 0.25), (1e4, 0.75)):
+        vth, a = O.vth_kms(T), O.damping_a(T)
+        p += w * np.real(wofz(-v / vth + 1j * a)) / np.sqrt(np.pi) / vth
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (p[1:] + p[:-1]) * np.diff(v))])
+    p_bins = np.diff(np.interp(edges, v, cdf))
+    counts = r["spec"].astype(float)
+    m = p_bins * N > 5
+    chi2 = np.sum((counts[m] - N * p_bins[m]) ** 2 / (N * p_bins[m]))
+    assert stats.chi2.sf(chi2, np.count_nonzero(m) - 1) > 1e-3

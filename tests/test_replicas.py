@@ -15,24 +15,28 @@ from paper_1409_4480_gb300 import replicas
 from paper_1409_4480_gb300 import synth as S
 
 
-def _spec():
+def _spec(diffuse=False):
     return S.RunSpec(n_packets=1001, seed=77, albedo=0.32, spec_units=1, spec_lo=-400, spec_hi=400, spec_nbins=40,
-                     cameras=S.axis_cameras(4), cam_lo=-400, cam_hi=400, cam_nbins=20)
+                     cameras=S.axis_cameras(4), cam_lo=-400, cam_hi=400, cam_nbins=20, source=int(diffuse))
 
 
-def _grid():
-    return S.sphere(10, 1e4, 1e4, v_max_kms=60.0, tau_dust=0.8)
+def _grid(diffuse=False):
+    g = S.sphere(10, 1e4, 1e4, v_max_kms=60.0, tau_dust=0.8)
+    if diffuse:
+        # diffuse emission in proportion to n^2 (recombination-like)
+        g.lum = np.asarray(g.n_HI, np.float64) ** 2 + 1e-3
+    return g
 
 
-def _rank_main(rank, world, port, outdir):
+def _rank_main(rank, world, port, outdir, diffuse=False):
     import oracle as O
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    spec = _spec()
+    spec = _spec(diffuse)
     first, n = replicas.packet_range(spec.n_packets, rank, world)
     spec.n_packets, spec.pid_offset = n, first
-    r = O.run(_grid(), spec, images=True)
+    r = O.run(_grid(diffuse), spec, images=True)
     tot = replicas.allreduce_tallies(r)
     if rank == 0:
         np.savez(os.path.join(outdir, "sum.npz"), **{k: np.asarray(tot[k]) for k in
@@ -58,10 +62,12 @@ def test_packet_range_partitions():
         replicas.packet_range(10, 2, 2)
 
 
-def test_two_gloo_replicas_sum_to_the_whole(O, tmp_path):
-    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+@pytest.mark.parametrize("diffuse", [False, True])
+def test_two_gloo_replicas_sum_to_the_whole(O, tmp_path, diffuse):
+    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path), diffuse), nprocs=2, join=True,
+                       start_method="spawn")
     got = np.load(tmp_path / "sum.npz")
-    whole = O.run(_grid(), _spec(), images=True)
+    whole = O.run(_grid(diffuse), _spec(diffuse), images=True)
     for k in replicas.INT_KEYS:
         assert np.array_equal(got[k], np.asarray(whole[k])), k
     for k in replicas.FLOAT_KEYS:
