@@ -1,4 +1,4 @@
-// Persistent photon-packet transport kernel (Cartesian grids).
+// Persistent photon-packet transport kernel (Cartesian and octree grids).
 //
 // Paper mapping:
 //   emission           Sec. 3.1.1 (isotropic k_i, x_i = 0 in the source cell, or
