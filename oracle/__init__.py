@@ -49,7 +49,7 @@ class Params(C.Structure):
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double),
                 ("cam_nbins", C.c_int), ("fov_half", C.c_double), ("n_threads", C.c_int),
                 ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p),
-                ("pid0", C.c_uint64), ("emission", C.c_int), ("source", C.c_int)]
+                ("pid0", C.c_uint64), ("emission", C.c_int), ("source", C.c_int), ("exact", C.c_int)]
 
 
 class Result(C.Structure):
@@ -67,7 +67,7 @@ class ScatterIO(C.Structure):
                 ("atau0", C.c_double), ("phase", C.c_int), ("pid", C.c_uint64), ("event", C.c_uint32),
                 ("x_f", C.c_double), ("k_f", C.c_double * 3), ("u_atom", C.c_double * 3),
                 ("u_par", C.c_double), ("x_crit", C.c_double), ("RQ", C.c_double), ("mu", C.c_double),
-                ("n_trials", C.c_int)]
+                ("n_trials", C.c_int), ("exact", C.c_int)]
 
 
 def _setup(L):
@@ -89,6 +89,7 @@ def _setup(L):
     L.o_uniform.argtypes = [C.c_uint32]
     L.o_scatter_many.argtypes = [P, sz, P]
     L.o_sample_upar_many.argtypes = [d, d, C.c_uint64, C.c_uint32, P, P, P, sz]
+    L.o_sample_upar_many_ex.argtypes = [d, d, C.c_uint64, C.c_uint32, P, P, P, sz, C.c_int]
     L.o_sample_mu_many.argtypes = [d, P, P, sz]
     L.o_atau_nl.restype = C.c_int
     L.o_atau_nl.argtypes = [P, d, P]
@@ -150,11 +151,14 @@ def uniform(r):
     return np.array([lib().o_uniform(int(v)) for v in np.asarray(r, np.uint32).ravel()])
 
 
-def sample_upar(x, a, n, seed=1, pid0=0, event=1):
+def sample_upar(x, a, n, seed=1, pid0=0, event=1, exact=False):
+    """n draws of u_par at frequency x (packet ids pid0 + i); exact: the
+    exact-physics mode (|x| >= 9 by numeric inversion of Eq. uparf)."""
     out = np.empty(n, np.float64)
     ntr = np.empty(n, np.int32)
     k = _key(seed)
-    lib().o_sample_upar_many(float(x), float(a), int(pid0), int(event), _ptr(k), _ptr(out), _ptr(ntr), n)
+    lib().o_sample_upar_many_ex(float(x), float(a), int(pid0), int(event), _ptr(k), _ptr(out), _ptr(ntr), n,
+                                int(bool(exact)))
     return out, ntr
 
 
@@ -234,9 +238,12 @@ def octree_locate(g, pos, direction):
     return int(lib().o_octree_locate(C.byref(s), _ptr(p), _ptr(d)))
 
 
-def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False, pid0: int = 0) -> dict:
+def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False, pid0: int = 0,
+        exact: bool = False) -> dict:
     """Full packet loop on grid g with run description spec (synth.RunSpec);
-    packets are ids pid0 .. pid0 + spec.n_packets - 1."""
+    packets are ids pid0 .. pid0 + spec.n_packets - 1.  exact: the
+    exact-physics mode (quadrature H, exact far-wing u_par), for measuring
+    the bias of the approximations."""
     s, keep = _grid_struct(g)
     p = Params()
     p.pid0 = int(pid0) + int(getattr(spec, "pid_offset", 0) or 0)
@@ -253,6 +260,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     p.max_scatter = int(spec.max_scatter)
     p.emission = int(getattr(spec, "emission", 0) or 0)
     p.source = int(getattr(spec, "source", 0) or 0)
+    p.exact = int(bool(exact))
     p.spec_units = int(spec.spec_units)
     p.T_ref = float(spec.T_ref)
     p.spec_lo, p.spec_hi, p.spec_nbins = float(spec.spec_lo), float(spec.spec_hi), int(spec.spec_nbins)

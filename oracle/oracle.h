@@ -65,6 +65,8 @@ typedef struct {
   double RQ;         /* R/Q drawn for the phase function                       */
   double mu;         /* cos(theta) between k_i and k_f                         */
   int    n_trials;   /* rejection trials used for u_par                        */
+  /* in */
+  int    exact;      /* exact-physics mode: |x| >= 9 by numeric inversion      */
 } o_scatter_io;
 
 /* One resonant (HI) scattering, Sec. 3.1.3 + 3.2.3 + 3.2.4, with the RNG
@@ -80,6 +82,8 @@ double o_sample_upar(double x, double a, uint64_t pid, uint32_t event,
 double o_sample_mu(double RQ, double u);
 void   o_sample_upar_many(double x, double a, uint64_t pid0, uint32_t event,
                           const uint32_t key[2], double* out, int32_t* ntr, size_t n);
+void   o_sample_upar_many_ex(double x, double a, uint64_t pid0, uint32_t event, const uint32_t key[2],
+                             double* out, int32_t* ntr, size_t n, int exact);
 void   o_sample_mu_many(double RQ, const double* u, double* mu, size_t n);
 
 /* ---------------------------------------------------------------- grid -- */
@@ -140,6 +144,11 @@ typedef struct {
   uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
   int       emission;       /* 0 line centre (x = 0), 1 natural + thermal        */
   int       source;         /* 0 point (src_pos, src_sigma), 1 cells by luminosity */
+  int       exact;          /* exact-physics mode, for measuring the bias of the
+                               approximations: H(a,x) by quadrature instead of
+                               H_approx, and u_par at |x| >= 9 by numeric
+                               inversion instead of the Gaussian (core-skipping
+                               and recoil are the run's own switches)        */
 } o_params;
 
 typedef struct {

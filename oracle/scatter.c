@@ -17,7 +17,9 @@
  *   - every u_par regime test uses |x|; the draw is made for |x| and the sign
  *     of u_par is flipped when x < 0, since f(-x,u) = f(x,-u) (Sec. 3.2.3);
  *   - x >= 9 draws a Gaussian of mean 1/|x| and variance 1/2 (the width of
- *     exp(-u^2)); no rejection step there;
+ *     exp(-u^2)); no rejection step there.  In the exact-physics mode (used
+ *     to measure the approximations' bias) it is instead the numeric
+ *     inversion of Eq. uparf itself;
  *   - the piecewise proposal picks theta in [theta0, pi/2] when p < R and in
  *     [-pi/2, theta0] otherwise; acceptance is exp(-u^2) on the lower piece
  *     and exp(u0^2 - u^2) on the upper one, accepted when R' < acceptance;
@@ -42,17 +44,49 @@ static void draw_block(const uint32_t key[2], uint64_t pid, uint32_t event, uint
   for (int i = 0; i < 4; ++i) u[i] = o_uniform(r[i]);
 }
 
+/* Exact-physics mode, |x| >= 9: u_par from the distribution of Eq. uparf,
+ * f(u) ~ exp(-u^2) / ((|x| - u)^2 + a^2), by inverting its CDF numerically:
+ * the CDF by the trapezoid rule on O_EXACT_N intervals of [-8, 8] (beyond,
+ * exp(-u^2) < 2e-28 and |x| - u >= 1), inverted at R by linear interpolation
+ * inside the interval that holds R (error O(h^2), h = 16 / O_EXACT_N). */
+#define O_EXACT_N 16384
+static double sample_upar_inverse(double xa, double a, double R) {
+  double cdf[O_EXACT_N + 1];
+  const double L = 8.0, h = 2.0 * L / O_EXACT_N;
+  double u = -L, fprev = exp(-u * u) / ((xa - u) * (xa - u) + a * a);
+  cdf[0] = 0.0;
+  for (int i = 1; i <= O_EXACT_N; ++i) {
+    u = -L + i * h;
+    double f = exp(-u * u) / ((xa - u) * (xa - u) + a * a);
+    cdf[i] = cdf[i - 1] + 0.5 * h * (fprev + f);
+    fprev = f;
+  }
+  double target = R * cdf[O_EXACT_N];
+  int lo = 1, hi = O_EXACT_N;             /* first i with cdf[i] >= target */
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    if (cdf[mid] >= target) hi = mid; else lo = mid + 1;
+  }
+  double w = cdf[lo] - cdf[lo - 1];
+  double frac = w > 0.0 ? (target - cdf[lo - 1]) / w : 0.5;
+  return -L + (lo - 1 + frac) * h;
+}
+
 /* Sec. 3.2.3.  Returns u_par for frequency x; *n_trials gets the number of
  * proposals drawn (O_MAX_TRIALS + 1 when the cap was hit). */
 static double sample_upar(double x, double a, double x_cw, const uint32_t key[2],
-                          uint64_t pid, uint32_t event, int* n_trials) {
+                          uint64_t pid, uint32_t event, int* n_trials, int exact) {
   double xa = fabs(x);
   double u = 0.0;
   double R[4];
   if (xa >= 9.0) {
-    /* far wing: Gaussian with its peak shifted to 1/x */
     draw_block(key, pid, event, 2, R);
-    u = 1.0 / xa + sqrt(-log(R[0])) * cos(2.0 * O_PI * R[1]);
+    if (exact) {
+      u = sample_upar_inverse(xa, a, R[0]);
+    } else {
+      /* far wing: Gaussian with its peak shifted to 1/x */
+      u = 1.0 / xa + sqrt(-log(R[0])) * cos(2.0 * O_PI * R[1]);
+    }
     *n_trials = 1;
   } else if (xa <= 1.0) {
     /* small |x|: Lorentzian comparison function g ~ 1/(a^2 + (x-u)^2),
@@ -92,7 +126,7 @@ static double sample_upar(double x, double a, double x_cw, const uint32_t key[2]
 
 double o_sample_upar(double x, double a, uint64_t pid, uint32_t event,
                      const uint32_t key[2], int* n_trials) {
-  return sample_upar(x, a, o_x_cw_fit(a), key, pid, event, n_trials);
+  return sample_upar(x, a, o_x_cw_fit(a), key, pid, event, n_trials, 0);
 }
 
 /* Eq. phaseW: CDF of W(mu) ~ 1 + RQ mu^2 on [-1,1] is
@@ -139,7 +173,7 @@ void o_scatter_hi(o_scatter_io* s, const uint32_t key[2]) {
 
   /* parallel velocity (Sec. 3.2.3) */
   int ntr = 0;
-  double upar = sample_upar(x, a, x_cw, key, s->pid, s->event, &ntr);
+  double upar = sample_upar(x, a, x_cw, key, s->pid, s->event, &ntr, s->exact);
   s->n_trials = ntr;
   s->u_par = upar;
 
@@ -172,14 +206,19 @@ void o_scatter_many(o_scatter_io* s, size_t n, const uint32_t key[2]) {
 
 /* Batched draws for distribution pins: sample i uses packet id pid0 + i,
  * event index `event`. */
-void o_sample_upar_many(double x, double a, uint64_t pid0, uint32_t event,
-                        const uint32_t key[2], double* out, int32_t* ntr, size_t n) {
+void o_sample_upar_many_ex(double x, double a, uint64_t pid0, uint32_t event, const uint32_t key[2],
+                           double* out, int32_t* ntr, size_t n, int exact) {
   double x_cw = o_x_cw_fit(a);
   for (size_t i = 0; i < n; ++i) {
     int t = 0;
-    out[i] = sample_upar(x, a, x_cw, key, pid0 + i, event, &t);
+    out[i] = sample_upar(x, a, x_cw, key, pid0 + i, event, &t, exact);
     if (ntr) ntr[i] = t;
   }
+}
+
+void o_sample_upar_many(double x, double a, uint64_t pid0, uint32_t event,
+                        const uint32_t key[2], double* out, int32_t* ntr, size_t n) {
+  o_sample_upar_many_ex(x, a, pid0, event, key, out, ntr, n, 0);
 }
 
 void o_sample_mu_many(double RQ, const double* u, double* mu, size_t n) {

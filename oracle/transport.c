@@ -77,6 +77,11 @@ typedef struct {
   uint64_t lum_total;
 } worker;
 
+/* H(a,x): App. A1's approximation, or the quadrature in the exact-physics mode */
+static double H_of(const o_params* p, double a, double x) {
+  return p->exact ? o_H_exact(a, x) : o_H_approx(a, x);
+}
+
 static void draw_block(const uint32_t key[2], uint64_t pid, uint32_t event, uint32_t blk, double u[4]) {
   uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), event, blk};
   uint32_t r[4];
@@ -133,7 +138,7 @@ static void peel(worker* w, int cam, const double r0[3], int64_t c0, double x_c,
     o_cell_bounds(g, c, clo, chi);
     int ax;
     double l = o_exit_distance(clo, chi, r, k, &ax);
-    double H = o_H_approx(g->a[c], x);
+    double H = H_of(p, g->a[c], x);
     tau += (g->kHI[c] * H + g->kd[c]) * l;
     w->n_peel++;
     if (tau > p->tau_esc_max) return;
@@ -266,7 +271,7 @@ static void run_packet(worker* w, uint64_t idx) {
       o_cell_bounds(g, c, clo, chi);
       int ax;
       double l = o_exit_distance(clo, chi, r, k, &ax);
-      double ktot = g->kHI[c] * o_H_approx(g->a[c], x) + g->kd[c];
+      double ktot = g->kHI[c] * H_of(p, g->a[c], x) + g->kd[c];
       double tau_cell = ktot * l;
       w->n_cell++;
       if (tau <= tau_cell) {
@@ -292,7 +297,7 @@ static void run_packet(worker* w, uint64_t idx) {
     /* interaction, event e */
     ++event;
     draw_block(w->key, pid, event, 0, B0);
-    double H = o_H_approx(g->a[c], x);
+    double H = H_of(p, g->a[c], x);
     double ktot = g->kHI[c] * H + g->kd[c];
     if (B0[0] * ktot < g->kd[c]) {
       /* dust */
@@ -317,6 +322,7 @@ static void run_packet(worker* w, uint64_t idx) {
       else
         s.atau0 = -1.0;
       s.phase = p->phase;
+      s.exact = p->exact;
       s.pid = pid;
       s.event = event;
       o_scatter_hi(&s, w->key);
