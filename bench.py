@@ -363,7 +363,12 @@ def run_gpu(args):
                                   "p99": float(np.percentile(lat_sorted, 99)), "n_requests": len(lat),
                                   "arrivals": "burst: all steps' requests submitted at t0"},
             "plain": {"value": plain_scat / (plain_ms / 1e3), "unit": UNIT, "kernel_ms": plain_ms,
-                      "wall_s": plain_wall, "path": "colt_run_batch, one blocking launch of the 9 solves"},
+                      "wall_s": plain_wall, "path": "colt_run_batch, one blocking launch of the 9 solves",
+                      "cell_visits_per_s": visits[0] / (plain_ms / 1e3),
+                      "peel_visits_per_s": visits[1] / (plain_ms / 1e3),
+                      "record_bytes_per_visit": 32,
+                      "dram_bytes_per_visit": (traffic / max(visits[0] + visits[1], 1)
+                                               if traffic is not None else None)},
             "config": {"workload": WORKLOAD,
                        "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200} km/s, tau_d=1, A=0.32",
                        "packets_per_case_per_step": B, "steps_per_job": PACKETS_PER_CASE_JOB // B,
