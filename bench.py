@@ -14,8 +14,9 @@ value      scatterings/s (executed, core-skipped ones not counted) of the
            persistent launches in flight; p50/p99 request latency beside it
 plain      the same steps through the blocking single-launch call
            (colt_run_batch), one step
-e2e        one step through colt_create_grid (host fields) + colt_submit +
-           colt_read_result (spectra and image cubes back to the host)
+e2e        the same number of steps through colt_create_grid (every step's
+           grids from host fields) + colt_submit + colt_read_result (every
+           solve's spectra and image cubes back to the host)
 --impl reference   the FP64 CPU oracle on the host cores, bounded samples
 --single-case I    one blocking solve of case I (profiling driver)
 
@@ -30,6 +31,10 @@ serving   256 requests (spheres or slabs on 64^3 grids, tau0, T, v_max, dust
           and packet counts drawn per request, seeds 4000 + i) arriving as a
           Poisson process at 75% of the throughput measured on the same mix
           submitted at once; reports throughput and p50/p99 latency
+halo_diffuse  the halo emitting from its ionised gas (recombination +
+          collisional excitation per leaf)
+tslab     the temperature suites of uniform slabs (fixed tau0, fixed column)
+galaxies  the 16 idealized first-galaxy models with the flux-table observables
 """
 import argparse
 import json
@@ -311,36 +316,68 @@ def run_gpu(args):
     plain_ms = res_plain[0]["kernel_ms"]
     visits = (res_plain[0]["n_cell_visits"], res_plain[0]["n_peel_visits"], res_plain[0]["n_peel_rays"])
 
-    # end to end: host fields -> grids -> served solves -> results (spectra + images) on the host
+    # end to end: host fields -> grids -> served solves -> results (spectra + images) on the host,
+    # over as many steps as the device-timed value (each step uploads its own grids and reads its
+    # own results back); a failure there falls back to one step
     e2e = None
     if not args.no_e2e:
         s_e2e = s_plain + 1
-        h2d = d2h = 0
-        ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev2.record(stream)
-        ghs = [C.colt_create_grid(ctx, g) for g in grids_h]
-        h2d = sum(6 * 4 * g.n_cells for g in grids_h)
-        off = (s_e2e * world + rank) * B
-        sps = [case_spec(i, B, off, images=img) for i in range(9)]
-        rids = [C.colt_submit(ctx, ghs[i], sp) for i, sp in enumerate(sps)]
-        e2e_scat = 0
-        for rid, sp in zip(rids, sps):
-            C.colt_wait(ctx, rid, -1.0)
-        for rid, sp in zip(rids, sps):
-            r = C.colt_read_result(ctx, rid, sp) if not img else read_with_images(C, ctx, rid, sp)
-            e2e_scat += r["n_scat"]
-            d2h += sum(v.nbytes for k, v in r.items() if isinstance(v, np.ndarray))
-            C.colt_release(ctx, rid)
-        for gh in ghs:
-            C.colt_destroy_grid(ctx, gh)
-        ev3.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = ev2.elapsed_time(ev3)
-        e2e = {"value": e2e_scat / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "path": "colt_create_grid (host fields) -> colt_submit -> colt_wait -> colt_read_result "
-                       "(escape + camera spectra + image cubes) -> colt_destroy_grid"}
+
+        def e2e_leg(n_steps):
+            h2d = d2h = 0
+            scat = 0
+            made, rids = [], []
+            ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev2.record(stream)
+            try:
+                steps = []
+                for s in range(n_steps):
+                    ghs = [C.colt_create_grid(ctx, g) for g in grids_h]
+                    made += ghs
+                    h2d += sum(6 * 4 * g.n_cells for g in grids_h)
+                    steps.append(ghs)
+                for s, ghs in enumerate(steps):
+                    off = ((s_e2e + s) * world + rank) * B
+                    for i, gh in enumerate(ghs):
+                        sp = case_spec(i, B, off, images=img)
+                        rids.append((C.colt_submit(ctx, gh, sp), sp))
+                for rid, sp in rids:
+                    C.colt_wait(ctx, rid, -1.0)
+                while rids:
+                    rid, sp = rids.pop(0)
+                    r = C.colt_read_result(ctx, rid, sp) if not img else read_with_images(C, ctx, rid, sp)
+                    scat += r["n_scat"]
+                    d2h += sum(v.nbytes for k, v in r.items() if isinstance(v, np.ndarray))
+                    C.colt_release(ctx, rid)
+                for gh in made:
+                    C.colt_destroy_grid(ctx, gh)
+                made = []
+                ev3.record(stream)
+                torch.cuda.synchronize()
+            finally:
+                for rid, sp in rids:
+                    try:
+                        C.colt_wait(ctx, rid, -1.0)
+                        C.colt_release(ctx, rid)
+                    except C.ColtError:
+                        pass
+                for gh in made:
+                    try:
+                        C.colt_destroy_grid(ctx, gh)
+                    except C.ColtError:
+                        pass
+            e_ms = ev2.elapsed_time(ev3)
+            return {"value": scat / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d // n_steps,
+                    "d2h_bytes_per_step": d2h // n_steps, "ms_per_step": e_ms / n_steps, "steps": n_steps,
+                    "path": "colt_create_grid (host fields) -> colt_submit -> colt_wait -> colt_read_result "
+                            "(escape + camera spectra + image cubes) -> colt_destroy_grid, every step"}
+
+        try:
+            e2e = e2e_leg(args.steps)
+        except Exception as exc:          # noqa: BLE001 -- report, then measure one step
+            e2e = e2e_leg(1)
+            e2e["note"] = f"{args.steps}-step leg failed ({type(exc).__name__}); one step measured"
 
     # roofline of the transport kernel: FP32 issue-bound
     peaks = measured_peaks()
