@@ -56,6 +56,25 @@ def test_exact_and_approximate_spectra_agree(O):
     m = (a + b) > 0
     chi2 = np.sum((a[m] - b[m]) ** 2 / (a[m] + b[m]))
     assert stats.chi2.sf(chi2, np.count_nonzero(m) - 1) > 1e-3
-    # the exact mode really evaluates the quadrature: a thin slab of tau0 = 1 at
-    # x = 0 lets exp(-tau0 H(a,0)) of the packets through unscattered, with H(a,0) = erfcx(a)
+    # the quadrature H the exact mode evaluates is the Faddeeva value (here at line centre)
     assert np.real(wofz(1j * 0.0149)) == pytest.approx(O.H_exact(0.0149, 0.0), rel=1e-10)
+
+
+@pytest.mark.parametrize("x,a", [(9.0, 0.0149), (12.0, 4.702e-4), (30.0, 0.0149)])
+def test_far_wing_gaussian_ks_distance(O, x, a):
+    # Sec. 3.2.3 replaces Eq. uparf beyond |x| = 9 by a Gaussian of mean 1/|x|;
+    # its Kolmogorov-Smirnov distance to the exact distribution (reported) is
+    # within the sampling noise of 4e4 draws, ~0.005-0.01, from |x| = 9 on
+    grid = np.linspace(-6.0, 6.0, 24001)
+    f = np.exp(-grid ** 2) / ((x - grid) ** 2 + a * a)
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (f[1:] + f[:-1]) * np.diff(grid))])
+    cdf /= cdf[-1]
+    exact_cdf = lambda u: np.interp(u, grid, cdf)
+    n = 40000
+    ug, _ = O.sample_upar(x, a, n, seed=95)
+    d_gauss = stats.kstest(ug, exact_cdf).statistic
+    ue, _ = O.sample_upar(x, a, n, seed=96, exact=True)
+    d_exact = stats.kstest(ue, exact_cdf).statistic
+    print(f"x={x}: KS distance, Gaussian {d_gauss:.4f}, exact sampler {d_exact:.4f}")
+    assert d_gauss < 0.02
+    assert stats.kstest(ue, exact_cdf).pvalue > 1e-3
