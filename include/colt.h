@@ -292,7 +292,8 @@ int colt_release(colt_ctx* ctx, colt_req req);
  * Inputs: n solves (1 <= n <= 8; larger n returns COLT_EINVAL), each a
  * Cartesian grid given by its geometry and its DEVICE array of packed cell
  * records (8 floats per cell, the layout colt_read_cells returns, including
- * a tau_NL), and its run parameters (host).  Outputs: per solve, DEVICE
+ * a tau_NL), and its run parameters (host; source must be COLT_SOURCE_POINT,
+ * since a grid view has no luminosity table).  Outputs: per solve, DEVICE
  * tallies the caller allocated: spec [spec_nbins] and counters [8] (emitted,
  * escaped, absorbed, capped, scatterings, HI scatterings, underflow,
  * overflow) as unsigned 64-bit, cam_spec / cam_spec2 [n_cam * cam_nbins]
