@@ -8,7 +8,6 @@ CUDA library.  Functions here marshal numpy arrays into liboracle.so.
 from __future__ import annotations
 
 import ctypes as C
-import os
 
 import numpy as np
 

@@ -3,7 +3,6 @@ colt_read_spectrum / colt_read_image with continuous batching.  Each request's r
 equals its result alone (colt_run with the same grid and parameters):
 integer tallies bitwise, peel-off sums up to FP64 summation order.  Memory
 admission queues what does not fit and rejects what never can."""
-import time
 
 import numpy as np
 import pytest
