@@ -794,7 +794,9 @@ def main():
                     help="octree and galaxy workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.75)
-    ap.add_argument("--packets-per-case", type=int, default=125000)
+    ap.add_argument("--packets-per-case", type=int, default=None,
+                    help="packets per solve per step (default: 125000 for the sphere suite and --single-case; "
+                         "4096 halo / halo_diffuse / galaxies, 2048 cosmo, 20000 tslab)")
     ap.add_argument("--ref-packets", type=int, default=2048)
     ap.add_argument("--single-case", type=int, default=-1)
     ap.add_argument("--max-scatter", type=int, default=0)
@@ -807,6 +809,9 @@ def main():
     ap.add_argument("--flops-cell", type=float, default=45.0)
     ap.add_argument("--flops-scat", type=float, default=300.0)
     args = ap.parse_args()
+    if args.packets_per_case is None:
+        args.packets_per_case = {"halo": 4096, "halo_diffuse": 4096, "galaxies": 4096, "cosmo": 2048,
+                                 "tslab": 20000}.get(args.workload, 125000)
     if args.impl == "reference":
         run_reference(args)
     elif args.single_case >= 0:
