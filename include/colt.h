@@ -142,7 +142,9 @@ typedef struct {
 typedef struct {
   uint64_t n_packets;
   uint64_t seed;            /* Philox key; results depend only on (seed, packet id) */
-  double src_pos[3];        /* point source position (cm)                            */
+  double src_pos[3];        /* point source position (cm); several sources are several
+                               solves on the same grid (batched or served together),
+                               packets in proportion to their luminosities          */
   double src_sigma;         /* Gaussian spread of the source (cm), 0 = point          */
   int core_skip;            /* COLT_SKIP_* (Sec. 3.2.4); any other nonzero value is
                                rejected                                             */
