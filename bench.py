@@ -333,8 +333,10 @@ def run_gpu(args):
             try:
                 steps = []
                 for s in range(n_steps):
-                    ghs = [C.colt_create_grid(ctx, g) for g in grids_h]
-                    made += ghs
+                    ghs = []
+                    for g in grids_h:
+                        ghs.append(C.colt_create_grid(ctx, g))
+                        made.append(ghs[-1])        # released in `finally` if a later call fails
                     h2d += sum(6 * 4 * g.n_cells for g in grids_h)
                     steps.append(ghs)
                 for s, ghs in enumerate(steps):
