@@ -381,7 +381,7 @@ def run_gpu(args):
             e2e = e2e_leg(1)
             e2e["note"] = f"{args.steps}-step leg failed ({type(exc).__name__}); one step measured"
 
-    # roofline of the transport kernel: FP32 issue-bound
+    # roofline of the transport kernel: bound by FP32 issue (no dense contraction, records and tallies in L2)
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12
@@ -806,7 +806,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    # algorithmic FP32 operations per unit (the design doc derives them from the code)
+    # algorithmic FP32 operations per unit (peel-off visit, flight cell visit, scattering)
     ap.add_argument("--flops-peel", type=float, default=30.0)
     ap.add_argument("--flops-cell", type=float, default=45.0)
     ap.add_argument("--flops-scat", type=float, default=300.0)

@@ -308,7 +308,12 @@ int colt_release(colt_ctx* ctx, colt_req req);
  * The launch header, job table and counters live in one static device array
  * of 16 KB that every GPU loading the library keeps until process exit.  The
  * first call on a device looks up that array's device address with the
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process, so do not use this entry
+ * point across a device reset (or a release and re-creation of the primary
+ * context).  The solves run in the caller's order (colt_run_batch starts the
+ * grids with the longest past histories first; this call keeps no such
+ * per-grid record).  All calls
  * share the array, which keeps the last call's contents: calls that overlap
  * on the GPU (from several threads or streams) race, so serialise them. */
 typedef struct {

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcolt.so")
-SOURCES = ["transport.cu", "grid.cu", "parity.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["transport.cu", "grid.cu", "parity.cu", "api.cu", "noalloc.cu", "runparams.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -425,11 +425,65 @@ class DeviceTallies(C.Structure):
                 ("cam_spec2", C.c_void_p), ("cam_image", C.c_void_p)]
 
 
+def _noalloc_layout(name, t, dtype, numel):
+    """The C entry point takes bare device pointers and no lengths, so every
+    buffer is checked here: a wrong size, type or layout would make the
+    kernel read or write outside it."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: {t.numel()} elements, expected {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: not contiguous")
+
+
+def _noalloc_device(name, t):
+    import torch
+    if not t.is_cuda:
+        raise ValueError(f"{name}: not a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+
+
+def check_noalloc_args(grids, records, specs, tallies, images=False):
+    """Raise ValueError unless every records and tally tensor has the type,
+    layout and length colt_run_noalloc will access (all checked first) and
+    lies on the current CUDA device."""
+    import torch
+    n = len(grids)
+    if not (len(records) == len(specs) == len(tallies) == n):
+        raise ValueError("grids, records, specs and tallies must have the same length")
+    checked = []
+    for i, (g, rec, sp, t) in enumerate(zip(grids, records, specs, tallies)):
+        nx, ny, nz = [int(v) for v in g.shape]
+        want = [(f"records[{i}]", rec, torch.float32, nx * ny * nz * 8),
+                (f"tallies[{i}]['spec']", t.get("spec"), torch.int64, int(sp.spec_nbins)),
+                (f"tallies[{i}]['counters']", t.get("counters"), torch.int64, 8)]
+        ncam = len(sp.cameras)
+        if ncam:
+            want += [(f"tallies[{i}]['{f}']", t.get(f), torch.float64, ncam * int(sp.cam_nbins))
+                     for f in ("cam_spec", "cam_spec2")]
+            npx = sum(int(c.npix) ** 2 for c in sp.cameras) if images else 0
+            if npx:
+                want.append((f"tallies[{i}]['cam_image']", t.get("cam_image"), torch.float64,
+                             npx * int(sp.cam_nbins)))
+        for name, tensor, dtype, numel in want:
+            _noalloc_layout(name, tensor, dtype, numel)
+            checked.append((name, tensor))
+    for name, tensor in checked:
+        _noalloc_device(name, tensor)
+
+
 def colt_run_noalloc(grids, records, specs, tallies, cuda_stream=None, images=False):
     """Blocking solve(s) without device allocation.  grids: synth.Grid list
     (geometry only); records: device tensors (8 floats per cell); tallies:
     dicts of device tensors spec, counters, cam_spec, cam_spec2, cam_image.
-    Returns the C status code (0 = COLT_OK)."""
+    Every tensor is checked (ValueError) before the call.  Returns the C status
+    code (0 = COLT_OK)."""
+    check_noalloc_args(grids, records, specs, tallies, images)
     n = len(grids)
     gv = (GridView * n)()
     ps = (RunParams * n)()

@@ -25,6 +25,7 @@
 
 #include "colt.h"
 #include "internal.h"
+#include "runparams.h"
 
 using namespace colt;
 
@@ -168,53 +169,9 @@ int cuda_fail(colt_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
-// --- Sec. 2 line constants (T4 = T / 1e4 K) for the per-cell records ------
-inline double vth_kms(double T) { return 12.85 * std::sqrt(T / 1.0e4); }
-inline double damping_a(double T) { return 4.702e-4 / std::sqrt(T / 1.0e4); }
-inline double sigma0(double T) { return 5.898e-14 / std::sqrt(T / 1.0e4); }
-
-int camera_axis(const double d[3], int* axis, int* sgn) {
-  int nz = 0, ax = -1;
-  for (int a = 0; a < 3; ++a) {
-    if (d[a] != 0.0) { ++nz; ax = a; }
-  }
-  if (nz != 1 || std::fabs(d[ax]) != 1.0) return -1;
-  *axis = ax;
-  *sgn = d[ax] > 0 ? 1 : -1;
-  return 0;
-}
-
 int validate_params(colt_ctx* ctx, const colt_run_params* p, const GridObj& g) {
-  if (p->core_skip != COLT_SKIP_OFF && p->core_skip != COLT_SKIP_CELL_NL && p->core_skip != COLT_SKIP_JEANS)
-    return fail(ctx, COLT_EINVAL, "bad core_skip mode");
-  if (p->source != COLT_SOURCE_POINT && p->source != COLT_SOURCE_CELLS) return fail(ctx, COLT_EINVAL, "bad source");
-  if (p->source == COLT_SOURCE_CELLS && !g.lum_cum)
-    return fail(ctx, COLT_EINVAL, "COLT_SOURCE_CELLS needs colt_set_cell_luminosity on the grid");
-  if (!p) return fail(ctx, COLT_EINVAL, "params is NULL");
-  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo)) return fail(ctx, COLT_EINVAL, "bad escape-spectrum bins");
-  if (p->n_cam < 0 || p->n_cam > kMaxCams) return fail(ctx, COLT_EINVAL, "n_cam must be in [0, 8]");
-  if (p->n_cam > 0) {
-    if (!p->cams) return fail(ctx, COLT_EINVAL, "cams is NULL");
-    if (p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)) return fail(ctx, COLT_EINVAL, "bad camera bins");
-    for (int i = 0; i < p->n_cam; ++i) {
-      int ax, s;
-      if (camera_axis(p->cams[i].dir, &ax, &s)) return fail(ctx, COLT_EINVAL, "camera direction must be a coordinate axis");
-      if (p->cams[i].npix < 0 || p->cams[i].npix > 65536) return fail(ctx, COLT_EINVAL, "bad npix");
-    }
-  }
-  if (p->precision != COLT_PLAIN && p->precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
-  if (p->phase != COLT_PHASE_DIPOLE && p->phase != COLT_PHASE_ISOTROPIC) return fail(ctx, COLT_EINVAL, "bad phase");
-  if (p->emission != COLT_EMIT_LINE_CENTRE && p->emission != COLT_EMIT_NATURAL_THERMAL)
-    return fail(ctx, COLT_EINVAL, "bad emission mode");
-  if (p->spec_units != COLT_UNITS_X && p->spec_units != COLT_UNITS_DV_KMS) return fail(ctx, COLT_EINVAL, "bad spec_units");
-  if (p->n_cam > 0 && p->cam_units != COLT_UNITS_X && p->cam_units != COLT_UNITS_DV_KMS)
-    return fail(ctx, COLT_EINVAL, "bad cam_units");
-  if ((p->spec_units == COLT_UNITS_X || (p->n_cam > 0 && p->cam_units == COLT_UNITS_X)) && !(p->T_ref > 0))
-    return fail(ctx, COLT_EINVAL, "T_ref must be > 0 for x units");
-  if (!(p->tau_esc_max > 0)) return fail(ctx, COLT_EINVAL, "tau_esc_max must be > 0");
-  if (!(p->albedo >= 0 && p->albedo <= 1)) return fail(ctx, COLT_EINVAL, "albedo must be in [0,1]");
-  if (!(p->src_sigma >= 0)) return fail(ctx, COLT_EINVAL, "src_sigma must be >= 0");
-  return COLT_OK;
+  const char* msg = check_run_params(p, g.lum_cum != nullptr);
+  return msg ? fail(ctx, COLT_EINVAL, msg) : COLT_OK;
 }
 
 size_t tally_bytes(const colt_run_params* p, bool per_packet) {
@@ -268,51 +225,7 @@ void free_tally(Tally* t) {
 }
 
 // Job description from a grid and parameters (tally pointers attached later).
-RunDev make_run(const GridObj& g, const colt_run_params* p) {
-  RunDev r;
-  r.n_packets = p->n_packets;
-  r.pid_offset = p->pid_offset;
-  r.rng = Rng{uint32_t(p->seed), uint32_t(p->seed >> 32)};
-  for (int a = 0; a < 3; ++a) r.src[a] = p->src_pos[a];
-  r.src_sigma = p->src_sigma;
-  r.core_skip = p->core_skip;
-  r.recoil = p->recoil ? 1 : 0;
-  r.phase = p->phase;
-  r.emission = p->emission;
-  r.source = p->source;
-  r.jeans_c = jeans_coefficient();
-  r.jeans_cf = (float)r.jeans_c;
-  r.tau_max = p->tau_esc_max;
-  r.albedo = p->albedo;
-  r.max_scatter = p->max_scatter;
-  const double vref = p->T_ref > 0 ? vth_kms(p->T_ref) : 1.0;
-  r.spec_scale = p->spec_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
-  r.spec_lo = p->spec_lo;
-  r.spec_hi = p->spec_hi;
-  r.spec_nb = p->spec_nbins;
-  r.n_cam = p->n_cam;
-  int64_t off = 0;
-  for (int i = 0; i < p->n_cam; ++i) {
-    camera_axis(p->cams[i].dir, &r.cam[i].axis, &r.cam[i].sgn);
-    r.cam[i].npix = p->cams[i].npix;
-    r.cam[i].img_off = off;
-    off += (int64_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
-  }
-  r.cam_scale = p->cam_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
-  r.cam_lo = p->cam_lo;
-  r.cam_hi = p->cam_hi;
-  r.cam_nb = p->cam_nbins > 0 ? p->cam_nbins : 1;
-  double fov = 0;
-  for (int a = 0; a < 3; ++a) {
-    r.centre[a] = 0.5 * (g.dev.lo[a] + g.dev.hi[a]);
-    fov = std::max(fov, 0.5 * (g.dev.hi[a] - g.dev.lo[a]));
-  }
-  r.fov_half = p->fov_half > 0 ? p->fov_half : fov;
-  r.pix_scale = 0.5 / r.fov_half;
-  r.cam_inv_width = p->cam_hi > p->cam_lo ? (double)r.cam_nb / (p->cam_hi - p->cam_lo) : 1.0;
-  fill_f32(r);
-  return r;
-}
+RunDev make_run(const GridObj& g, const colt_run_params* p) { return make_run_dev(g.dev.lo, g.dev.hi, p); }
 
 void attach_tally(RunDev* r, const Tally& t) {
   r->t.spec = t.spec;

@@ -13,6 +13,7 @@
 
 #include "colt.h"
 #include "internal.h"
+#include "runparams.h"
 
 using namespace colt;
 
@@ -42,7 +43,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 namespace {
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current).
+// device (with that device current) and kept for the life of the process: a
+// device reset, or a release and re-creation of the primary context, may move
+// the symbol, so this entry point must not be used across either.
 int scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return COLT_EINVAL;
   std::lock_guard<std::mutex> lk(g_setup_mu);
@@ -53,16 +56,6 @@ int scratch_address(int device, unsigned char** out) {
   }
   *out = g_scratch_dev[device];
   return COLT_OK;
-}
-
-bool axis_of(const double d[3], int* axis, int* sgn) {
-  int nz = 0, ax = -1;
-  for (int a = 0; a < 3; ++a)
-    if (d[a] != 0.0) { ++nz; ax = a; }
-  if (nz != 1 || (d[ax] != 1.0 && d[ax] != -1.0)) return false;
-  *axis = ax;
-  *sgn = d[ax] > 0 ? 1 : -1;
-  return true;
 }
 
 }  // namespace
@@ -94,18 +87,12 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     const colt_run_params& p = params[i];
     const colt_device_tallies& t = tallies[i];
     if (!gv.records || gv.nx <= 0 || gv.ny <= 0 || gv.nz <= 0) return COLT_EINVAL;
-    if (p.precision != precision || (p.precision != COLT_PLAIN && p.precision != COLT_MIXED)) return COLT_EINVAL;
-    if (p.emission != COLT_EMIT_LINE_CENTRE && p.emission != COLT_EMIT_NATURAL_THERMAL) return COLT_EINVAL;
-    if (p.core_skip != COLT_SKIP_OFF && p.core_skip != COLT_SKIP_CELL_NL && p.core_skip != COLT_SKIP_JEANS)
-      return COLT_EINVAL;
-    if (p.source != COLT_SOURCE_POINT) return COLT_EINVAL;   // a grid view carries no luminosity table
-    if (p.spec_nbins <= 0 || !(p.spec_hi > p.spec_lo) || !t.spec || !t.counters) return COLT_EINVAL;
-    if (p.n_cam < 0 || p.n_cam > kMaxCams) return COLT_EINVAL;
-    if (p.n_cam > 0 && (!p.cams || p.cam_nbins <= 0 || !(p.cam_hi > p.cam_lo) || !t.cam_spec || !t.cam_spec2))
-      return COLT_EINVAL;
-    if (!(p.tau_esc_max > 0) || !(p.albedo >= 0 && p.albedo <= 1) || !(p.src_sigma >= 0)) return COLT_EINVAL;
-    if ((p.spec_units == COLT_UNITS_X || (p.n_cam > 0 && p.cam_units == COLT_UNITS_X)) && !(p.T_ref > 0))
-      return COLT_EINVAL;
+    // the same parameter checks as colt_run, plus the limits of a grid view
+    if (check_run_params(&p, false) != nullptr || p.precision != precision) return COLT_EINVAL;
+    if (!t.spec || !t.counters) return COLT_EINVAL;
+    if (p.n_cam > 0 && (!t.cam_spec || !t.cam_spec2)) return COLT_EINVAL;
+    for (int c = 0; c < p.n_cam; ++c)
+      if (p.cams[c].npix > 0 && !t.cam_image) return COLT_EINVAL;
     GridDev& G = jobs[i].g;
     G = GridDev{};
     G.rec = reinterpret_cast<const float4*>(gv.records);
@@ -122,49 +109,8 @@ extern "C" int colt_run_noalloc(int n, const colt_grid_view* grids, const colt_r
     G.periodic_xy = gv.periodic_xy ? 1 : 0;
     G.n_cells = (int64_t)gv.nx * gv.ny * gv.nz;
     RunDev& r = jobs[i].p;
-    r = RunDev{};
-    r.n_packets = p.n_packets;
-    r.pid_offset = p.pid_offset;
-    r.rng = Rng{uint32_t(p.seed), uint32_t(p.seed >> 32)};
-    for (int a = 0; a < 3; ++a) r.src[a] = p.src_pos[a];
-    r.src_sigma = p.src_sigma;
-    r.core_skip = p.core_skip;
-    r.jeans_c = jeans_coefficient();
-    r.jeans_cf = (float)r.jeans_c;
-    r.recoil = p.recoil ? 1 : 0;
-    r.phase = p.phase;
-    r.emission = p.emission;
+    r = make_run_dev(G.lo, G.hi, &p);
     extras = extras || run_needs_extras(r);
-    r.tau_max = p.tau_esc_max;
-    r.albedo = p.albedo;
-    r.max_scatter = p.max_scatter;
-    const double vref = p.T_ref > 0 ? 12.85 * std::sqrt(p.T_ref / 1.0e4) : 1.0;   // v_th at T_ref, Sec. 2
-    r.spec_scale = p.spec_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
-    r.spec_lo = p.spec_lo;
-    r.spec_hi = p.spec_hi;
-    r.spec_nb = p.spec_nbins;
-    r.n_cam = p.n_cam;
-    int64_t off = 0;
-    for (int c = 0; c < p.n_cam; ++c) {
-      if (!axis_of(p.cams[c].dir, &r.cam[c].axis, &r.cam[c].sgn)) return COLT_EINVAL;
-      if (p.cams[c].npix < 0 || (p.cams[c].npix > 0 && !t.cam_image)) return COLT_EINVAL;
-      r.cam[c].npix = p.cams[c].npix;
-      r.cam[c].img_off = off;
-      off += (int64_t)p.cams[c].npix * p.cams[c].npix * p.cam_nbins;
-    }
-    r.cam_scale = p.cam_units == COLT_UNITS_X ? 1.0 / vref : -1.0;
-    r.cam_lo = p.cam_lo;
-    r.cam_hi = p.cam_hi;
-    r.cam_nb = p.cam_nbins > 0 ? p.cam_nbins : 1;
-    r.cam_inv_width = p.cam_hi > p.cam_lo ? (double)r.cam_nb / (p.cam_hi - p.cam_lo) : 1.0;
-    double fov = 0;
-    for (int a = 0; a < 3; ++a) {
-      r.centre[a] = 0.5 * (G.lo[a] + G.hi[a]);
-      fov = fov > 0.5 * (G.hi[a] - G.lo[a]) ? fov : 0.5 * (G.hi[a] - G.lo[a]);
-    }
-    r.fov_half = p.fov_half > 0 ? p.fov_half : fov;
-    r.pix_scale = 0.5 / r.fov_half;
-    fill_f32(r);
     r.t.spec = t.spec;
     r.t.counters = t.counters;
     r.t.cam_spec = t.cam_spec;

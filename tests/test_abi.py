@@ -72,3 +72,30 @@ def test_no_cpu_fallback_in_product_path():
                     txt = fh.read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_noalloc_binding_rejects_bad_buffers_before_calling():
+    # colt_run_noalloc takes bare pointers and no lengths: the binding checks
+    # every tensor first (these CPU tensors never reach the library)
+    import pytest
+    import torch
+    from paper_1409_4480_gb300 import colt
+    from paper_1409_4480_gb300 import synth as S
+    g = S.uniform_box((4, 4, 4), (-1e18,) * 3, (1e18,) * 3, 1e-3, 1e4)
+    spec = S.RunSpec(n_packets=10, seed=1, cameras=S.axis_cameras(0), cam_nbins=20)
+    good = dict(spec=torch.zeros(spec.spec_nbins, dtype=torch.int64),
+                counters=torch.zeros(8, dtype=torch.int64),
+                cam_spec=torch.zeros((6, 20), dtype=torch.float64),
+                cam_spec2=torch.zeros((6, 20), dtype=torch.float64))
+    short = torch.zeros(g.n_cells * 8 - 1, dtype=torch.float32)
+    with pytest.raises(ValueError, match="records.*elements"):
+        colt.colt_run_noalloc([g], [short], [spec], [good])
+    with pytest.raises(ValueError, match="dtype"):
+        colt.colt_run_noalloc([g], [torch.zeros(g.n_cells * 8, dtype=torch.float64)], [spec], [good])
+    with pytest.raises(ValueError, match="cam_spec2.*elements"):
+        colt.colt_run_noalloc([g], [torch.zeros(g.n_cells * 8)], [spec],
+                              [{**good, "cam_spec2": torch.zeros(6 * 20 - 1, dtype=torch.float64)}])
+    with pytest.raises(ValueError, match="counters"):
+        colt.colt_run_noalloc([g], [torch.zeros(g.n_cells * 8)], [spec], [{**good, "counters": None}])
+    with pytest.raises(ValueError, match="not a CUDA tensor"):
+        colt.colt_run_noalloc([g], [torch.zeros(g.n_cells * 8)], [spec], [good])

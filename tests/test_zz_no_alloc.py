@@ -4,7 +4,8 @@ call cudaMalloc for its user).  The caller owns the cell records and the
 tallies; the entry point keeps its launch header and counters in a static
 device array.  Its results must equal colt_run's on the same grid and
 parameters -- integer tallies exactly, peel-off sums up to FP64 summation
-order -- on two calls in a row (the shared array is reused).
+order -- on two calls in a row (the shared array is reused), and the second
+call must leave the device's free memory unchanged.
 
 This file is collected last on purpose."""
 import numpy as np
@@ -35,10 +36,18 @@ def test_noalloc_matches_colt_run_twice(colt):
              cam_spec=torch.ones((6, spec.cam_nbins), dtype=torch.float64, device=dev),
              cam_spec2=torch.ones((6, spec.cam_nbins), dtype=torch.float64, device=dev),
              cam_image=torch.ones((6 * 8 * 8 * spec.cam_nbins,), dtype=torch.float64, device=dev))
-    for _ in range(2):
+    for call in range(2):
+        torch.cuda.synchronize()
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         rc = colt.colt_run_noalloc([g], [rec], [spec], [t], images=True)
         assert rc == colt.COLT_OK
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call (module loading, launch resources), a call
+            # takes no device memory: the driver's free bytes and torch's
+            # allocator both stay where they were
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
         cnt = t["counters"].cpu().numpy().astype(np.uint64)
         assert cnt[0] == ref["n_emitted"] == 6000
         assert (cnt[1], cnt[2], cnt[3]) == (ref["n_escaped"], ref["n_absorbed"], ref["n_capped"])
