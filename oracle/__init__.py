@@ -94,6 +94,12 @@ def _setup(L):
     L.o_atau_nl.argtypes = [P, d, P]
     L.o_run.restype = C.c_int
     L.o_run.argtypes = [P, P, P]
+    L.o_prepare.restype = C.c_void_p
+    L.o_prepare.argtypes = [P, P]
+    L.o_run_prepared.restype = C.c_int
+    L.o_run_prepared.argtypes = [P, P, P]
+    L.o_prepared_free.restype = None
+    L.o_prepared_free.argtypes = [P]
     L.o_octree_locate.restype = C.c_int64
     L.o_octree_locate.argtypes = [P, P, P]
 
@@ -237,13 +243,8 @@ def octree_locate(g, pos, direction):
     return int(lib().o_octree_locate(C.byref(s), _ptr(p), _ptr(d)))
 
 
-def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False, pid0: int = 0,
-        exact: bool = False) -> dict:
-    """Full packet loop on grid g with run description spec (synth.RunSpec);
-    packets are ids pid0 .. pid0 + spec.n_packets - 1.  exact: the
-    exact-physics mode (quadrature H, exact far-wing u_par), for measuring
-    the bias of the approximations."""
-    s, keep = _grid_struct(g)
+def _params(g, spec, n_threads, per_packet, images, pid0, exact):
+    """(o_params, keep-alive list, output dict, o_result) for one run."""
     p = Params()
     p.pid0 = int(pid0) + int(getattr(spec, "pid_offset", 0) or 0)
     p.n_packets = int(spec.n_packets)
@@ -276,6 +277,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     p.fov_half = float(fov)
     p.n_threads = int(n_threads)
     out = {}
+    keep = [cams]
     if per_packet:
         out["pk_status"] = np.zeros(spec.n_packets, np.int32)
         out["pk_nscat"] = np.zeros(spec.n_packets, np.uint64)
@@ -285,6 +287,7 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
     r = Result()
     spec_arr = np.zeros(spec.spec_nbins, np.uint64)
     r.spec = _ptr(spec_arr)
+    out["spec"] = spec_arr
     if ncam:
         cs = np.zeros((ncam, spec.cam_nbins), np.float64)
         cs2 = np.zeros((ncam, spec.cam_nbins), np.float64)
@@ -296,13 +299,75 @@ def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = Fa
             img = np.zeros(sum(n * n for n in npx) * spec.cam_nbins, np.float64)
             r.cam_image = _ptr(img)
             out["cam_image"] = img
-    rc = lib().o_run(C.byref(s), C.byref(p), C.byref(r))
-    if rc:
-        raise ValueError(f"oracle run rejected its inputs ({rc})")
-    out.update(spec=spec_arr, n_emitted=r.n_emitted, n_escaped=r.n_escaped, n_absorbed=r.n_absorbed,
+    return p, keep, out, r
+
+
+def _outputs(out, r):
+    out.update(n_emitted=r.n_emitted, n_escaped=r.n_escaped, n_absorbed=r.n_absorbed,
                n_capped=r.n_capped, n_scat=r.n_scat, n_scat_hi=r.n_scat_hi,
                n_cell_visits=r.n_cell_visits, n_peel_visits=r.n_peel_visits,
                spec_under=r.spec_under, spec_over=r.spec_over, seconds=r.seconds,
                transport_seconds=r.transport_seconds,
                n_threads=r.n_threads_used)
     return out
+
+
+def run(g, spec, n_threads: int = 0, per_packet: bool = False, images: bool = False, pid0: int = 0,
+        exact: bool = False) -> dict:
+    """Full packet loop on grid g with run description spec (synth.RunSpec);
+    packets are ids pid0 .. pid0 + spec.n_packets - 1.  exact: the
+    exact-physics mode (quadrature H, exact far-wing u_par), for measuring
+    the bias of the approximations."""
+    s, keep = _grid_struct(g)
+    p, keep2, out, r = _params(g, spec, n_threads, per_packet, images, pid0, exact)
+    rc = lib().o_run(C.byref(s), C.byref(p), C.byref(r))
+    if rc:
+        raise ValueError(f"oracle run rejected its inputs ({rc})")
+    return _outputs(out, r)
+
+
+def run_many(g, specs, images: bool = False, workers: int = 4, per_packet: bool = False) -> list:
+    """Several runs on one grid derivation: the grid's cell quantities (and
+    a tau_NL, luminosity weights) are derived once for specs[0], whose
+    core_skip, f_nl and source every spec must share, and the runs proceed
+    `workers` at a time (each on its share of the host threads), so that the
+    longest histories of one run overlap the others."""
+    import os
+    import threading
+    s, keep = _grid_struct(g)
+    p0, keep0, _, _ = _params(g, specs[0], 0, False, False, 0, False)
+    pg = lib().o_prepare(C.byref(s), C.byref(p0))
+    if not pg:
+        raise ValueError("oracle grid rejected")
+    workers = max(1, min(workers, len(specs)))
+    nthr = max(1, (os.cpu_count() or 1) // workers)
+    results = [None] * len(specs)
+    errors = []
+    nxt = [0]
+    mu = threading.Lock()
+
+    def worker():
+        while True:
+            with mu:
+                i = nxt[0]
+                nxt[0] += 1
+            if i >= len(specs) or errors:
+                return
+            p, kp, out, r = _params(g, specs[i], nthr, per_packet, images, 0, False)
+            rc = lib().o_run_prepared(C.c_void_p(pg), C.byref(p), C.byref(r))
+            if rc:
+                errors.append(ValueError(f"oracle run rejected its inputs ({rc})"))
+                return
+            results[i] = _outputs(out, r)
+
+    try:
+        ths = [threading.Thread(target=worker) for _ in range(workers)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+    finally:
+        lib().o_prepared_free(C.c_void_p(pg))
+    if errors:
+        raise errors[0]
+    return results

@@ -174,6 +174,17 @@ int  o_atau_nl(const o_grid_in* g, double f_nl, double* out);
 /* Full packet loop (Sec. 3.1 + 3.2 + 6.1). Returns 0 or a negative code. */
 int  o_run(const o_grid_in* g, const o_params* p, o_result* r);
 
+/* The same in two steps, so that several runs share one grid derivation:
+ * o_prepare derives the cell quantities (plus a tau_NL when p->core_skip == 1
+ * and the luminosity weights when p->source == 1; NULL on bad input), and
+ * o_run_prepared runs p's packets on it (p must agree with the prepared
+ * core_skip, f_nl and source; several calls may run at once on one prepared
+ * grid, which they only read). */
+typedef struct o_prepared o_prepared;
+o_prepared* o_prepare(const o_grid_in* g, const o_params* p);
+int  o_run_prepared(const o_prepared* pg, const o_params* p, o_result* r);
+void o_prepared_free(o_prepared* pg);
+
 /* Octree helpers exposed for parity tests of the walk (kind == 1 grids). */
 int64_t o_octree_locate(const o_grid_in* g, const double pos[3], const double dir[3]);
 

@@ -374,41 +374,71 @@ static void* worker_main(void* arg) {
   return NULL;
 }
 
-int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
+/* A derived grid (cell quantities, a tau_NL when core_skip == 1, the
+ * luminosity weights when source == 1), reusable by several runs whose
+ * parameters agree on core_skip, f_nl and source. */
+struct o_prepared {
+  o_grid g;
+  int core_skip, source;
+  double f_nl;
+  uint64_t* lum_cum;
+  uint64_t lum_total;
+  double seconds;
+};
+
+o_prepared* o_prepare(const o_grid_in* gin, const o_params* p) {
   struct timespec t0, t1;
   clock_gettime(CLOCK_MONOTONIC, &t0);
-  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo) || !res->spec) return -1;
-  if (p->n_cam < 0 || (p->n_cam > 0 && (!p->cams || p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)))) return -1;
-  o_grid g;
-  int rc = o_grid_build(gin, &g);
-  if (rc) return rc;
-  if (p->core_skip == 1) o_atau_nl_grid(&g, p->f_nl);
+  o_prepared* pg = (o_prepared*)calloc(1, sizeof(o_prepared));
+  if (!pg) return NULL;
+  if (o_grid_build(gin, &pg->g)) { free(pg); return NULL; }
+  pg->core_skip = p->core_skip;
+  pg->source = p->source;
+  pg->f_nl = p->f_nl;
+  if (p->core_skip == 1) o_atau_nl_grid(&pg->g, p->f_nl);
   /* diffuse emission: integer weights w_c = floor(2^s L_c / max L) with
    * s = 63 - b, b the least integer with 2^b >= n_cells + 1 (the weights then
    * sum below 2^63), and their inclusive prefix sums */
-  uint64_t* lum_cum = NULL;
-  uint64_t lum_total = 0;
   if (p->source == 1) {
-    int64_t n = g.n_cells;
-    if (!gin->lum) { o_grid_free(&g); return -1; }
+    int64_t n = pg->g.n_cells;
     double lmax = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-      if (!(gin->lum[i] >= 0.0) || !isfinite(gin->lum[i])) { o_grid_free(&g); return -1; }
-      if (gin->lum[i] > lmax) lmax = gin->lum[i];
+    int ok = gin->lum != NULL;
+    for (int64_t i = 0; ok && i < n; ++i) {
+      if (!(gin->lum[i] >= 0.0) || !isfinite(gin->lum[i])) ok = 0;
+      else if (gin->lum[i] > lmax) lmax = gin->lum[i];
     }
-    if (!(lmax > 0.0)) { o_grid_free(&g); return -1; }
+    if (!ok || !(lmax > 0.0)) { o_prepared_free(pg); return NULL; }
     int b = 0;
     while (b < 63 && ((uint64_t)1 << b) < (uint64_t)n + 1) ++b;
-    lum_cum = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
+    pg->lum_cum = (uint64_t*)malloc((size_t)n * sizeof(uint64_t));
     for (int64_t i = 0; i < n; ++i) {
-      lum_total += (uint64_t)floor(ldexp(gin->lum[i] / lmax, 63 - b));
-      lum_cum[i] = lum_total;
+      pg->lum_total += (uint64_t)floor(ldexp(gin->lum[i] / lmax, 63 - b));
+      pg->lum_cum[i] = pg->lum_total;
     }
   } else if (p->source != 0) {
-    o_grid_free(&g);
-    return -1;
+    o_prepared_free(pg);
+    return NULL;
   }
-  struct timespec tm;
+  clock_gettime(CLOCK_MONOTONIC, &t1);
+  pg->seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
+  return pg;
+}
+
+void o_prepared_free(o_prepared* pg) {
+  if (!pg) return;
+  free(pg->lum_cum);
+  o_grid_free(&pg->g);
+  free(pg);
+}
+
+int o_run_prepared(const o_prepared* pg, const o_params* p, o_result* res) {
+  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo) || !res->spec) return -1;
+  if (p->n_cam < 0 || (p->n_cam > 0 && (!p->cams || p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)))) return -1;
+  if (p->source != pg->source || (p->core_skip == 1) != (pg->core_skip == 1) ||
+      (p->core_skip == 1 && p->f_nl != pg->f_nl))
+    return -1;
+  const o_grid* gp = &pg->g;
+  struct timespec tm, t1;
   clock_gettime(CLOCK_MONOTONIC, &tm);
   int nt = p->n_threads;
   if (nt <= 0) nt = (int)sysconf(_SC_NPROCESSORS_ONLN);
@@ -420,11 +450,11 @@ int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
   size_t ncs = (size_t)(p->n_cam > 0 ? p->n_cam : 0) * (size_t)(p->cam_nbins > 0 ? p->cam_nbins : 0);
   for (int t = 0; t < nt; ++t) {
     worker* w = &ws[t];
-    w->g = &g; w->p = p; w->res = res;
+    w->g = gp; w->p = p; w->res = res;
     w->key[0] = (uint32_t)p->seed; w->key[1] = (uint32_t)(p->seed >> 32);
     w->vth_ref = o_vth_kms(p->T_ref > 0.0 ? p->T_ref : 1.0e4);
     w->tid = t; w->nthreads = nt; w->img_lock = &lock;
-    w->lum_cum = lum_cum; w->lum_total = lum_total;
+    w->lum_cum = pg->lum_cum; w->lum_total = pg->lum_total;
     w->spec = (uint64_t*)calloc((size_t)p->spec_nbins, sizeof(uint64_t));
     if (ncs) {
       w->cam_spec = (double*)calloc(ncs, sizeof(double));
@@ -466,12 +496,21 @@ int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
     free(w->img_idx); free(w->img_w);
   }
   free(ws); free(th);
-  free(lum_cum);
   pthread_mutex_destroy(&lock);
-  o_grid_free(&g);
   clock_gettime(CLOCK_MONOTONIC, &t1);
   res->n_threads_used = nt;
-  res->seconds = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
   res->transport_seconds = (double)(t1.tv_sec - tm.tv_sec) + 1e-9 * (double)(t1.tv_nsec - tm.tv_nsec);
+  res->seconds = res->transport_seconds;
   return 0;
+}
+
+int o_run(const o_grid_in* gin, const o_params* p, o_result* res) {
+  if (p->spec_nbins <= 0 || !(p->spec_hi > p->spec_lo) || !res->spec) return -1;
+  if (p->n_cam < 0 || (p->n_cam > 0 && (!p->cams || p->cam_nbins <= 0 || !(p->cam_hi > p->cam_lo)))) return -1;
+  o_prepared* pg = o_prepare(gin, p);
+  if (!pg) return -1;
+  int rc = o_run_prepared(pg, p, res);
+  if (rc == 0) res->seconds = pg->seconds + res->transport_seconds;
+  o_prepared_free(pg);
+  return rc;
 }
