@@ -696,6 +696,13 @@ def serving_requests(n):
     return out
 
 
+def serving_grid(q):
+    """The 64^3 sphere or slab of one serving-mix request."""
+    if q["geom"] == "sphere":
+        return S.sphere(64, q["T"], q["tau0"], v_max_kms=q["v"], tau_dust=q["td"])
+    return S.slab(64, q["T"], q["tau0"], v_max_kms=q["v"], tau_dust=q["td"])
+
+
 def run_serving(args):
     """Poisson arrivals into the continuous-batching scheduler."""
     import torch
@@ -705,11 +712,7 @@ def run_serving(args):
     stream = torch.cuda.Stream()
     ctx = C.colt_init(local, 0, stream.cuda_stream)
     reqs = serving_requests(args.requests)
-    grids = []
-    for q in reqs:
-        g = S.sphere(64, q["T"], q["tau0"], v_max_kms=q["v"], tau_dust=q["td"]) if q["geom"] == "sphere" else \
-            S.slab(64, q["T"], q["tau0"], v_max_kms=q["v"], tau_dust=q["td"])
-        grids.append(C.colt_create_grid(ctx, g))
+    grids = [C.colt_create_grid(ctx, serving_grid(q)) for q in reqs]
     specs = [S.RunSpec(n_packets=q["n"], seed=q["seed"], albedo=0.32, spec_units=1, spec_lo=-q["w"], spec_hi=q["w"],
                        spec_nbins=200, precision=1, pid_offset=rank * q["n"]) for q in reqs]
 

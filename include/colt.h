@@ -259,6 +259,8 @@ typedef struct {
   uint64_t packets_done, packets_total;
   double submit_to_done_ms; /* latency, valid when done                          */
   uint64_t ctx_launches;    /* transport kernel launches this context has issued */
+  int cancelled;            /* 1 after colt_cancel: the tallies cover packets_done
+                               packets (those that had started), not packets_total */
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);
@@ -281,6 +283,15 @@ int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, siz
  * size (COLT_EINVAL otherwise). */
 int colt_read_image(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t n);
 int colt_read_result(colt_ctx* ctx, colt_req req, colt_result* out);
+/* Stop a request early.  A queued request is dropped at once (done, no
+ * tallies: reading its results gives zero counters).  An admitted one hands
+ * out no further packets: the packets already in a launch finish (a serving
+ * launch carries at most 2^20 packets), then the request is done with the
+ * tallies of those packets (colt_stats.cancelled = 1, packets_done < packets_total
+ * when it was cut short).  A done request is left as it is.  Never blocks. */
+int colt_cancel(colt_ctx* ctx, colt_req req);
+/* Free a finished or queued request's results (COLT_EAGAIN while it runs:
+ * colt_cancel first, then wait). */
 int colt_release(colt_ctx* ctx, colt_req req);
 
 /* --------------------------------------------- solve without allocating -- */

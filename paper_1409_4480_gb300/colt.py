@@ -30,7 +30,7 @@ COLT_SOURCE_POINT, COLT_SOURCE_CELLS = 0, 1
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
            "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
-           "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity"]
+           "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity", "colt_cancel"]
 
 _LIB = None
 
@@ -78,7 +78,7 @@ class Result(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("done", C.c_int), ("admitted", C.c_int), ("packets_done", C.c_uint64),
                 ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double),
-                ("ctx_launches", C.c_uint64)]
+                ("ctx_launches", C.c_uint64), ("cancelled", C.c_int)]
 
 
 class LaunchConfig(C.Structure):
@@ -130,6 +130,7 @@ def lib():
             "colt_read_image": (I, [P, U64, I, P, SZ]),
             "colt_read_result": (I, [P, U64, P]),
             "colt_release": (I, [P, U64]),
+            "colt_cancel": (I, [P, U64]),
             "colt_voigt": (I, [P, P, P, P, SZ, I, I]),
             "colt_scatter": (I, [P, P, SZ, U64, I]),
             "colt_run_noalloc": (I, [I, P, P, P, P]),
@@ -384,7 +385,8 @@ def colt_poll(ctx, req: int) -> dict:
     st = Stats()
     _check(ctx, lib().colt_poll(ctx, C.c_uint64(req), C.byref(done), C.byref(st)))
     return dict(done=bool(done.value), admitted=bool(st.admitted), packets_done=st.packets_done,
-                packets_total=st.packets_total, latency_ms=st.submit_to_done_ms, launches=st.ctx_launches)
+                packets_total=st.packets_total, latency_ms=st.submit_to_done_ms, launches=st.ctx_launches,
+                cancelled=bool(st.cancelled))
 
 
 def colt_wait(ctx, req: int, timeout_ms: float = -1.0):
@@ -408,6 +410,10 @@ def colt_read_result(ctx, req: int, spec) -> dict:
     r, out = _result_arrays(spec, False, False)
     _check(ctx, lib().colt_read_result(ctx, C.c_uint64(req), C.byref(r)))
     return _unpack(r, out)
+
+
+def colt_cancel(ctx, req: int):
+    _check(ctx, lib().colt_cancel(ctx, C.c_uint64(req)))
 
 
 def colt_release(ctx, req: int):

@@ -119,6 +119,8 @@ struct Req {
   int passed = 0;                       // launches built while it was ready but left out
   uint64_t next_local = 0;              // packets handed to launches
   uint64_t done_packets = 0;
+  uint64_t target = 0;                  // packets the request will run (n_packets, less after colt_cancel)
+  bool cancelled = false;
   double t_submit = 0, t_done = 0;
   size_t need_bytes = 0;
 };
@@ -565,7 +567,7 @@ int complete_slot(colt_ctx* ctx, int si) {
     Req& r = *it->second;
     learn_cost(ctx, r.grid, sl.lb.jmax_h[j]);
     r.done_packets += jp.second;
-    if (r.done_packets >= r.p.n_packets && r.state == kAdmitted) {
+    if (r.done_packets >= r.target && r.state == kAdmitted) {
       r.state = kDone;
       r.t_done = t;
     }
@@ -625,7 +627,7 @@ void CUDART_CB slot_done_cb(void* arg) {
 int serve_launch(colt_ctx* ctx, int si) {
   std::vector<Req*> act;
   for (auto& kv : ctx->reqs)
-    if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->p.n_packets)
+    if (kv.second->state == kAdmitted && kv.second->next_local < kv.second->target)
       act.push_back(kv.second.get());
   if (act.empty()) return 0;
   // requests passed over kMaxPassed times first (oldest first), then
@@ -664,7 +666,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   sl.jobs.clear();
   for (size_t i = 0; i < sel.size() && left > 0; ++i) {
     Req* r = sel[i];
-    const uint64_t rem = r->p.n_packets - r->next_local;
+    const uint64_t rem = r->target - r->next_local;
     const uint64_t fair = std::max<uint64_t>(1, left / (sel.size() - i));
     const uint64_t take = std::min<uint64_t>(rem, std::max<uint64_t>(fair, std::min<uint64_t>(rem, left)));
     if (take == 0) continue;
@@ -1101,6 +1103,7 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   if (grids_bytes + r->need_bytes > ctx->budget)
     return fail(ctx, COLT_ENOMEM, "request can never fit in the memory budget");
   r->run = make_run(it->second, &r->p);
+  r->target = r->p.n_packets;
   r->t_submit = now_ms();
   if (r->p.n_packets == 0) {
     r->state = kDone;
@@ -1130,6 +1133,32 @@ int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
     st->packets_total = r.p.n_packets;
     st->submit_to_done_ms = r.state == kDone ? r.t_done - r.t_submit : 0.0;
     st->ctx_launches = ctx->launches;
+    st->cancelled = r.cancelled ? 1 : 0;
+  }
+  return COLT_OK;
+}
+
+int colt_cancel(colt_ctx* ctx, colt_req req) {
+  if (!ctx) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  auto it = ctx->reqs.find(req);
+  if (it == ctx->reqs.end()) return fail(ctx, COLT_ENOTFOUND, "unknown request");
+  Req& r = *it->second;
+  if (r.state == kDone) return COLT_OK;
+  r.cancelled = true;
+  if (r.state == kQueued) {
+    // never admitted: no tallies, nothing on the device
+    ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), req), ctx->queue.end());
+    r.target = 0;
+    r.state = kDone;
+    r.t_done = now_ms();
+    return COLT_OK;
+  }
+  // admitted: packets already handed to launches finish; no more start
+  r.target = r.next_local;
+  if (r.done_packets >= r.target) {
+    r.state = kDone;
+    r.t_done = now_ms();
   }
   return COLT_OK;
 }

@@ -597,7 +597,14 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         // lab-frame escape frequency in FP64: Doppler velocity (x + k.u) v_th
         const double ku = (double)k[0] * r1.x + (double)k[1] * r1.y + (double)k[2] * r1.z;
         const double V = ((double)x + ku) / (double)r0.w;
-        finish(1, V * P.spec_scale);
+        if (isfinite(V) && isfinite((double)tau.value())) {
+          finish(1, V * P.spec_scale);
+        } else {
+          // only non-finite cell records (device records the host never
+          // checked) lead here: raise the device error flag, end as capped
+          atomicExch(L.error, 1);
+          finish(3, 0.0);
+        }
       } else if (interact) {
         ++event;
         // the event's first three draw blocks are independent: compute them
