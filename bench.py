@@ -1,40 +1,45 @@
 """Benchmark of the Lyman-alpha packet transport on one (or N) GB300.
 
-Workload (the 128^3 dusty-sphere suite): a uniform 128^3 sphere at T = 1e4 K,
-tau0 in {1e5, 1e6, 1e7}, Hubble-like velocity with v_max in {-200, 0, +200}
-km/s (nine cases), dust tau_d = 1 with albedo 0.32, peel-off to six axis
-cameras of 128^2 pixels x 200 bins over +-1000 km/s, 1e6 packets per case for
-the whole job.  A step is one batch of `--packets-per-case` packets of all nine
-cases (disjoint packet-id ranges per step and rank), mixed precision.
-Inputs are synthetic (seeded generators), resident in HBM before timing.
+Default run (`python bench.py [--gpus N --steps K --warmup W]`) prints ONE
+JSON line.  Its headline (value, e2e, roofline, cpu_baseline, clocks) is the
+largest workload:
 
-value      scatterings/s (executed, core-skipped ones not counted) of the
-           served form: every step's nine solves are submitted to the
-           continuous-batching scheduler (colt_submit), which keeps several
-           persistent launches in flight; p50/p99 request latency beside it
-plain      the same steps through the blocking single-launch call
-           (colt_run_batch), one step
-e2e        the same number of steps through colt_create_grid (every step's
-           grids from host fields) + colt_submit + colt_read_result (every
-           solve's spectra and image cubes back to the host)
---impl reference   the FP64 CPU oracle on the host cores, bounded samples
---single-case I    one blocking solve of case I (profiling driver)
+cosmo     the synthetic cosmological box (1 Mpc^3 comoving at z = 10,
+          lognormal density on an octree of 9.4e6 leaves, levels 7-12), five
+          sources at the highest density peaks, peel-off to three cameras of
+          512^2 pixels x 256 bins over +-1000 km/s, mixed precision.  A step is
+          one solve per source of --cosmo-packets packets (disjoint packet ids
+          per step and rank).  The K timed steps are submitted together to the
+          serving scheduler, as a user submits a job of many steps: its
+          persistent launches overlap, so one step's longest histories run
+          beside the other steps' work.  value = scatterings/s (executed,
+          core-skipped ones not counted) over the device-timed region (CUDA
+          events on the library's stream, grid resident); photons/s and served
+          p50/p99 beside it.  The same pass gives e2e: the grid built from host
+          fields, the K steps, and every solve's spectra and image cubes read
+          back to the host.  Warm-up steps run the same solves with histories
+          capped at 1e4 scatterings.
 
-Other workloads (--workload; the default is the sphere suite above):
-halo      the synthetic octree AMR halo (2.05e6 leaves, levels 6-12), packets
-          from a central Gaussian of 0.1 kpc, six 128^2 x 200 cameras; a step
-          is one solve of --packets-per-case packets
-cosmo     the synthetic cosmological octree box (1 Mpc^3 comoving at z = 10,
-          lognormal field, ~1e7 leaves), five sources at the highest peaks,
-          three 512^2 x 256 cameras; a step is five solves (one per source)
-serving   256 requests (spheres or slabs on 64^3 grids, tau0, T, v_max, dust
-          and packet counts drawn per request, seeds 4000 + i) arriving as a
+Secondary workloads, each with its own clocks (rank 0, N = 1), under
+"workloads":
+sphere128 the 128^3 dusty-sphere suite (tau0 {1e5,1e6,1e7} x v_max {-200,0,200}
+          km/s, dust tau 1, A = 0.32, six 128^2 x 200 cameras): served steps of
+          nine solves; the plain single-launch kernel on the whole job (1e6
+          packets per case in one launch); the plain FP64 kernel on one solve
+          (tau0 = 1e5 static, --fp64-packets)
+halo      the synthetic octree AMR halo (2.05e6 leaves, levels 6-12), central
+          Gaussian source of 0.1 kpc, six 128^2 x 200 cameras: served steps
+serving   256 requests (spheres or slabs on 64^3, tau0, T, v_max, dust and
+          packet counts drawn per request, seeds 4000 + i) arriving as a
           Poisson process at 75% of the throughput measured on the same mix
-          submitted at once; reports throughput and p50/p99 latency
-halo_diffuse  the halo emitting from its ionised gas (recombination +
-          collisional excitation per leaf)
-tslab     the temperature suites of uniform slabs (fixed tau0, fixed column)
-galaxies  the 16 idealized first-galaxy models with the flux-table observables
+          submitted at once; p50/p99 latency and throughput
+
+--impl reference  the FP64 CPU oracle on the host cores, bounded samples of the
+                  headline workload (one source's packets per step, cycling)
+--workload W      one workload alone (sphere128, halo, halo_diffuse, cosmo,
+                  serving, tslab, galaxies), for profiling
+--single-case I   one blocking solve of sphere-suite case I (profiling driver)
+--profile-case W  one short capped solve of workload W (ncu capture driver)
 """
 import argparse
 import json
@@ -128,30 +133,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_transport_sphere128_tau1e6_static_cap2000.md")
 KERNEL_SOURCES = ("paper_1409_4480_gb300/csrc/transport.cu", "paper_1409_4480_gb300/csrc/device.cuh",
-                  "paper_1409_4480_gb300/csrc/internal.h")
-
-
-def dram_bytes_per_scattering():
-    """DRAM bytes (read + write) per scattering of the transport kernel from the
-    committed ncu summary, or None when the kernel sources changed since that
-    capture (their sha256 is recorded in the summary)."""
-    import hashlib
-    import re
-    try:
-        text = open(TRAFFIC_PROFILE).read()
-    except OSError:
-        return None
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    m_hash = re.search(r"kernel_source_sha256: `([0-9a-f]+)`", text)
-    m_val = re.search(r"dram_bytes_per_unit: ([0-9.eE+-]+)", text)
-    if not m_hash or not m_val or m_hash.group(1) != h.hexdigest():
-        return None
-    return float(m_val.group(1))
+                  "paper_1409_4480_gb300/csrc/internal.h", "paper_1409_4480_gb300/csrc/octree.cuh",
+                  "paper_1409_4480_gb300/csrc/cellpos.cuh")
 
 
 def measured_peaks():
@@ -186,34 +170,37 @@ def oracle_sample(target_s=15.0, case=(1e6, 0.0), cores=0):
 
 
 def run_reference(args):
+    """The FP64 oracle, as it stands, on the host cores: each step a bounded
+    sample of the headline workload (--ref-packets packets of one source,
+    cycling through the five; camera spectra, no images), the grid derived
+    once; the packet loops timed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
-    cores = os.cpu_count()
-    t_all = 0.0
-    n_scat = 0
-    n_pk = 0
-    for s in range(args.warmup + args.steps):
-        t, v = cases()[s % 9]
-        g = case_grid(t, v)
-        spec = case_spec(s % 9, args.ref_packets, s * args.ref_packets, images=False)
-        r = O.run(g, spec)
-        if s >= args.warmup:
-            t_all += r["transport_seconds"]       # the packet loop; grids are inputs, as on the GPU
-            n_scat += r["n_scat"]
-            n_pk += args.ref_packets
+    g, srcs, cams, cnb, label = octree_workload("cosmo")
+    cams0 = [S.Camera(c.direction, 0) for c in cams]
+    n = args.ref_packets
+    specs = []
+    for st in range(args.warmup + args.steps):
+        j = st % len(srcs)
+        specs.append(cosmo_specs(srcs[j:j + 1], cams0, cnb, n, 10 ** 9 + st * n)[0])
+        specs[-1].seed = 300 + j
+    rs = O.run_many(g, specs, workers=1)
+    timed = rs[args.warmup:]
+    t_all = sum(r["transport_seconds"] for r in timed)
+    n_scat = sum(r["n_scat"] for r in timed)
     value = n_scat / t_all
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "photons_per_s": n_pk / t_all,
-            "config": {"workload": WORKLOAD, "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200}",
-                       "packets_per_step": args.ref_packets, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.ref_packets} packets per step, one case per step cycling "
-                                       f"through the 9 (6-camera peel-off spectra, no images); the packet loop "
-                                       f"timed, grid derivation excluded as on the GPU"},
+            "data": "synthetic", "photons_per_s": n * args.steps / t_all,
+            "config": {"workload": label, "packets_per_step": n, "sources": "one per step, cycling through the five",
+                       "cameras": "3 camera spectra x 256 bins (no images)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} packets per step of one source of {label}, cycling through the five "
+                                       f"sources; the packet loop timed on all host cores, grid derivation "
+                                       f"excluded as on the GPU"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -381,14 +368,7 @@ def run_gpu(args):
             e2e = e2e_leg(1)
             e2e["note"] = f"{args.steps}-step leg failed ({type(exc).__name__}); one step measured"
 
-    # roofline of the transport kernel: bound by FP32 issue (no dense contraction, records and tallies in L2)
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12
-    per_scat = ((args.flops_peel * visits[1] + args.flops_cell * visits[0]) / max(plain_scat, 1)) + args.flops_scat
-    achieved = per_scat * tot_scat / (ms / 1e3) / 1e12
-    dpb = dram_bytes_per_scattering()
-    traffic = dpb * plain_scat if dpb is not None else None
+    rf = roofline(profile_units("sphere128"), plain_scat, plain_ms, value, info)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.cpu_seconds)
@@ -405,9 +385,7 @@ def run_gpu(args):
                       "wall_s": plain_wall, "path": "colt_run_batch, one blocking launch of the 9 solves",
                       "cell_visits_per_s": visits[0] / (plain_ms / 1e3),
                       "peel_visits_per_s": visits[1] / (plain_ms / 1e3),
-                      "record_bytes_per_visit": 32,
-                      "dram_bytes_per_visit": (traffic / max(visits[0] + visits[1], 1)
-                                               if traffic is not None else None)},
+                      "record_bytes_per_visit": 32},
             "config": {"workload": WORKLOAD,
                        "cases": "tau0 {1e5,1e6,1e7} x v_max {-200,0,200} km/s, tau_d=1, A=0.32",
                        "packets_per_case_per_step": B, "steps_per_job": PACKETS_PER_CASE_JOB // B,
@@ -421,13 +399,7 @@ def run_gpu(args):
             "counts": {"scatterings": tot_scat, "packets": tot_pk,
                        "plain_step": {"scatterings": plain_scat, "cell_visits": visits[0], "peel_visits": visits[1],
                                       "peel_rays": visits[2]}},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": traffic,
-                         "traffic_unit": "DRAM bytes per step (one launch of the 9 solves), ncu bytes per "
-                                         "scattering of the committed capture x scatterings per step",
-                         "flops_per_scattering": per_scat,
-                         "peak_source": f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz "
-                                        f"(max SM clock, of measured)"},
+            "roofline": rf,
             "clocks": clk.summary(), "wall_s": wall}
     if e2e:
         line["e2e"] = e2e
@@ -770,12 +742,18 @@ def run_serving(args):
     C.colt_finalize(ctx)
 
 
-def launch_count(C, ctx, h):
+def launch_count(C, ctx, h=None):
     """Transport launches issued so far, read through a zero-packet request
-    (it completes at once and launches nothing)."""
+    (it completes at once and launches nothing) on grid h, or on a one-cell
+    grid made for the purpose."""
+    tmp = None
+    if h is None:
+        tmp = h = C.colt_create_grid(ctx, S.uniform_box((1, 1, 1), (-1.0,) * 3, (1.0,) * 3, 0.0, 1e4))
     rid = C.colt_submit(ctx, h, S.RunSpec(n_packets=0, seed=0))
     n = C.colt_poll(ctx, rid)["launches"]
     C.colt_release(ctx, rid)
+    if tmp is not None:
+        C.colt_destroy_grid(ctx, tmp)
     return n
 
 
@@ -787,40 +765,481 @@ def read_with_images(C, ctx, rid, sp):
     return C._unpack(r, out)
 
 
+# ------------------------------------------------------------------ suite --
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def kernel_source_hash():
+    """sha256 of the transport kernel's sources (a profile is current when it
+    names this hash)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_units(name):
+    """Per-scattering figures of the transport kernel on workload `name` from
+    its committed ncu summary (profiles/k_transport_<name>.md): FP32
+    operations (thread-level, FMA = 2) and DRAM bytes per executed
+    scattering, and the summary's file name; None when the summary is missing
+    or was taken on other kernel sources."""
+    import re
+    path = os.path.join(PROFILES, f"k_transport_{name}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256: `([0-9a-f]+)`", text)
+    if not m_hash or m_hash.group(1) != kernel_source_hash():
+        return None
+    out = {"profile": os.path.relpath(path, ROOT)}
+    for key in ("fp32_flop_per_scattering", "dram_bytes_per_scattering"):
+        m = re.search(key + r": ([0-9.eE+-]+)", text)
+        out[key] = float(m.group(1)) if m else None
+    return out
+
+
+def fp32_peak_tflops(info):
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    return info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12, sm_max
+
+
+def roofline(units, scat, kernel_ms, served_rate, info):
+    """`alu` roofline of the transport kernel: achieved = FP32 operations of
+    one launch (the profile's per-scattering count x the launch's executed
+    scatterings) / that launch's CUDA-event time; frac_served the same count
+    at the served scattering rate."""
+    peak, sm_max = fp32_peak_tflops(info)
+    src = f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz (max SM clock, of measured)"
+    if not units or units.get("fp32_flop_per_scattering") is None:
+        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "peak_source": src, "note": "no current ncu summary for this kernel"}
+    f = units["fp32_flop_per_scattering"]
+    achieved = f * scat / (kernel_ms * 1e-3) / 1e12
+    d = units.get("dram_bytes_per_scattering")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": d * scat if d is not None else None,
+            "traffic_unit": "DRAM bytes per launch (the profile's bytes per scattering x the launch's scatterings)",
+            "flop_per_scattering": f, "frac_served": f * served_rate / 1e12 / peak,
+            "launch": {"scatterings": scat, "kernel_ms": kernel_ms},
+            "profile": units["profile"], "peak_source": src}
+
+
+def served_burst(C, ctx, stream, reqs, read=None):
+    """Submit every (grid, spec) at once and wait for all: (device ms between
+    CUDA events on the library's stream around submit..done, wall s, results
+    of colt_read_result (or read(rid, spec)), per-request latency ms)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    ids = [(C.colt_submit(ctx, h, sp, images=read is not None), sp) for h, sp in reqs]
+    for rid, _ in ids:
+        C.colt_wait(ctx, rid, -1.0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out, lat = [], []
+    for rid, sp in ids:
+        st = C.colt_poll(ctx, rid)
+        lat.append(st["latency_ms"])
+        r = read(rid, sp) if read else C.colt_read_result(ctx, rid, S.RunSpec(**{**sp.__dict__, "cameras": []}))
+        out.append(r)
+        C.colt_release(ctx, rid)
+    return ev0.elapsed_time(ev1), wall, out, lat
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs, float), q)) if len(xs) else None
+
+
+def cosmo_specs(srcs, cams, cnb, B, off, cap=None):
+    out = []
+    for j, (pos, sig) in enumerate(srcs):
+        sp = S.RunSpec(n_packets=B, seed=300 + j, src_pos=pos, src_sigma=sig, albedo=0.32, spec_units=1,
+                       spec_lo=-1000.0, spec_hi=1000.0, spec_nbins=200, cameras=cams, cam_units=1,
+                       cam_lo=-1000.0, cam_hi=1000.0, cam_nbins=cnb, precision=1, pid_offset=off + j * B)
+        if cap:
+            sp.max_scatter = cap
+        out.append(sp)
+    return out
+
+
+def leg_cosmo(C, ctx, stream, args, info, world, rank):
+    """Headline: the cosmological box, K steps served together; e2e from the
+    same pass (grid from host fields .. results on the host)."""
+    import torch
+    g, srcs, cams, cnb, label = octree_workload("cosmo")
+    B = args.cosmo_packets
+    ns = len(srcs)
+
+    def step_specs(s, cap=None):
+        return cosmo_specs(srcs, cams, cnb, B, ((s * world + rank) * ns) * B, cap)
+    # warm-up on a grid of its own: tuning on capped histories, then W steps
+    # with histories capped at 1e4 scatterings
+    hw = C.colt_create_grid(ctx, g)
+    tuned = C.colt_autotune(ctx, hw, cosmo_specs(srcs[:1], S.axis_cameras(0, ("+x", "+y", "+z")), cnb,
+                                                 1 << 16, 1 << 40, cap=2000)[0])
+    served_burst(C, ctx, stream, [(hw, sp) for s in range(args.warmup) for sp in step_specs(s, cap=10000)])
+    C.colt_destroy_grid(ctx, hw)
+    launches0 = launch_count(C, ctx, None)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    # the timed pass: e2e region (events e0..e3, with host reads), device region (e1..e2)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    h2d = sum(4 * g.n_cells for _ in range(6)) + g.leaf_level.nbytes + g.leaf_ijk.nbytes
+    d2h = 0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        h = C.colt_create_grid(ctx, g)
+        torch.cuda.synchronize()
+        e[1].record(stream)
+        reqs = [(h, sp) for s in range(args.warmup, args.warmup + args.steps) for sp in step_specs(s)]
+        ids = [(C.colt_submit(ctx, hh, sp), sp) for hh, sp in reqs]
+        for rid, _ in ids:
+            C.colt_wait(ctx, rid, -1.0)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        scat = pk = 0
+        lat = []
+        for rid, sp in ids:
+            st = C.colt_poll(ctx, rid)
+            lat.append(st["latency_ms"])
+            r = read_with_images(C, ctx, rid, sp)
+            d2h += sum(v.nbytes for v in r.values() if isinstance(v, np.ndarray))
+            scat += r["n_scat"]
+            pk += r["n_emitted"]
+            del r
+            C.colt_release(ctx, rid)
+        C.colt_destroy_grid(ctx, h)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+    launches = launch_count(C, ctx, None) - launches0
+    ms = e[1].elapsed_time(e[2])
+    ms_e2e = e[0].elapsed_time(e[3])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0].item()), float(t[1].item())
+        c = torch.tensor([scat, pk], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        scat, pk = int(c[0].item()), int(c[1].item())
+    # one plain launch of one step (the dominant kernel's own time, for the roofline)
+    hp = C.colt_create_grid(ctx, g)
+    plain = C.colt_run_batch(ctx, [hp] * ns, step_specs(args.warmup + args.steps), images=True, outputs=False)
+    C.colt_destroy_grid(ctx, hp)
+    plain_scat = sum(r["n_scat"] for r in plain)
+    plain_ms = plain[0]["kernel_ms"]
+    value = scat / (ms * 1e-3)
+    units = profile_units("cosmo")
+    return {
+        "value": value, "photons_per_s": pk / (ms * 1e-3), "ms": ms, "scat": scat, "packets": pk,
+        "latency": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n_requests": len(lat),
+                    "arrivals": "burst: the K steps' solves submitted together"},
+        "e2e": {"value": scat / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
+                "d2h_bytes_per_step": int(d2h // args.steps), "ms_per_step": ms_e2e / args.steps,
+                "steps": args.steps,
+                "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit "
+                        "of every step -> colt_wait -> colt_read_result with escape spectra, camera spectra and "
+                        "image cubes -> colt_destroy_grid"},
+        "plain": {"value": plain_scat / (plain_ms * 1e-3), "unit": UNIT, "kernel_ms": plain_ms,
+                  "scatterings": plain_scat, "path": "colt_run_batch: one launch of one step's five solves"},
+        "roofline": roofline(units, plain_scat, plain_ms, value, info),
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "config": {"workload": label, "sources": ns, "packets_per_source_per_step": B,
+                   "cameras": "3 x 512^2 x 256 (+x, +y, +z)",
+                   "grid": f"octree, {g.n_cells} leaves, levels {int(g.leaf_level.min())}-{int(g.leaf_level.max())} "
+                           f"(refined on density; the workload description names levels 7-14, the density "
+                           f"criterion of this generator stops at 12)",
+                   "precision": "mixed (FP32 transport, FP32-pair position and tau, FP64 escape and tallies)",
+                   "launch": "served: the K steps submitted together, persistent launches in flight",
+                   "launch_config": dict(tuned, source="colt_autotune on one source, 65536 packets capped at "
+                                                       "2000 scatterings"),
+                   "warmup": "W steps with histories capped at 1e4 scatterings",
+                   "l2": "records 300 MB + octree tables 265 MB + tallies 1.6 GB per solve > 129 MB L2: "
+                         "inputs larger than L2"},
+    }
+
+
+def leg_sphere(C, ctx, stream, args, info):
+    """The 128^3 sphere suite: served steps, the plain launch of the whole
+    job, the plain FP64 kernel on one solve."""
+    grids = [case_grid(t, v) for t, v in cases()]
+    hs = [C.colt_create_grid(ctx, g) for g in grids]
+    B = 125000
+    tuned = C.colt_autotune(ctx, hs[4], case_spec(4, B, 0, images=False))
+
+    def specs_of(s):
+        return [case_spec(i, B, s * B, images=True) for i in range(9)]
+    served_burst(C, ctx, stream, [(hs[i], sp) for i, sp in enumerate(specs_of(0))])
+    with ClockSampler(0) as clk:
+        ms, wall, res, lat = served_burst(C, ctx, stream, [(hs[i], sp) for s in range(1, 1 + args.sphere_steps)
+                                                           for i, sp in enumerate(specs_of(s))])
+        scat = sum(r["n_scat"] for r in res)
+        pk = sum(r["n_emitted"] for r in res)
+        # plain: the whole job (1e6 packets per case) in one launch
+        job = [case_spec(i, PACKETS_PER_CASE_JOB, 10 ** 8, images=True) for i in range(9)]
+        plain = C.colt_run_batch(ctx, hs, job, images=True, outputs=False)
+        # plain FP64: one solve (tau0 = 1e5, static) alone
+        sp64 = case_spec(1, args.fp64_packets, 2 * 10 ** 8, images=True)
+        sp64.precision = 0
+        p64 = C.colt_run(ctx, hs[1], sp64)
+    for h in hs:
+        C.colt_destroy_grid(ctx, h)
+    plain_scat = sum(r["n_scat"] for r in plain)
+    plain_ms = plain[0]["kernel_ms"]
+    value = scat / (ms * 1e-3)
+    units = profile_units("sphere128")
+    return {"value": value, "unit": UNIT, "photons_per_s": pk / (ms * 1e-3), "steps": args.sphere_steps,
+            "ms_per_step": ms / args.sphere_steps,
+            "served_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n_requests": len(lat),
+                                  "arrivals": "burst"},
+            "plain": {"value": plain_scat / (plain_ms * 1e-3), "unit": UNIT, "kernel_ms": plain_ms,
+                      "scatterings": plain_scat, "packets": 9 * PACKETS_PER_CASE_JOB,
+                      "path": "colt_run_batch: the whole job (1e6 packets per case, nine cases) in one launch",
+                      "cell_visits": plain[0]["n_cell_visits"], "peel_visits": plain[0]["n_peel_visits"]},
+            "plain_fp64": {"value": p64["n_scat"] / (p64["kernel_ms"] * 1e-3), "unit": UNIT,
+                           "kernel_ms": p64["kernel_ms"], "packets": args.fp64_packets,
+                           "path": "colt_run, precision PLAIN: one solve (tau0 = 1e5, static) per launch"},
+            "roofline": roofline(units, plain_scat, plain_ms, value, info),
+            "clocks": clk.summary(),
+            "config": {"workload": WORKLOAD, "packets_per_case_per_step": B,
+                       "cameras": "6 x 128^2 x 200", "precision": "mixed (served, plain); FP64 (plain_fp64)",
+                       "launch_config": dict(tuned, source="colt_autotune on the tau0=1e6 static case"),
+                       "l2": "records 9 x 67 MB + tallies 9 x 157 MB per step > 129 MB L2"}}
+
+
+def leg_halo(C, ctx, stream, args, info):
+    g, srcs, cams, cnb, label = octree_workload("halo")
+    pos, sig = srcs[0]
+    h = C.colt_create_grid(ctx, g)
+    B = args.halo_packets
+
+    def spec(s, cap=None):
+        sp = S.RunSpec(n_packets=B, seed=300, src_pos=pos, src_sigma=sig, albedo=0.32, spec_units=1,
+                       spec_lo=-1000.0, spec_hi=1000.0, spec_nbins=200, cameras=cams, cam_units=1,
+                       cam_lo=-1000.0, cam_hi=1000.0, cam_nbins=cnb, precision=1, pid_offset=s * B)
+        if cap:
+            sp.max_scatter = cap
+        return sp
+    served_burst(C, ctx, stream, [(h, spec(0, cap=10000))])
+    with ClockSampler(0) as clk:
+        ms, wall, res, lat = served_burst(C, ctx, stream, [(h, spec(s)) for s in range(1, 1 + args.halo_steps)])
+    C.colt_destroy_grid(ctx, h)
+    scat = sum(r["n_scat"] for r in res)
+    pk = sum(r["n_emitted"] for r in res)
+    return {"value": scat / (ms * 1e-3), "unit": UNIT, "photons_per_s": pk / (ms * 1e-3), "steps": args.halo_steps,
+            "ms_per_step": ms / args.halo_steps,
+            "served_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n_requests": len(lat),
+                                  "arrivals": "burst"},
+            "clocks": clk.summary(),
+            "config": {"workload": label, "packets_per_step": B, "cameras": "6 x 128^2 x 200",
+                       "grid": f"octree, {g.n_cells} leaves, levels {int(g.leaf_level.min())}-"
+                               f"{int(g.leaf_level.max())}", "precision": "mixed",
+                       "launch": "served: the steps submitted together"}}
+
+
+def leg_serving(C, ctx, stream, args, n_req=256, load=0.75):
+    reqs = serving_requests(n_req)
+    grids = [C.colt_create_grid(ctx, serving_grid(q)) for q in reqs]
+    specs = [S.RunSpec(n_packets=q["n"], seed=q["seed"], albedo=0.32, spec_units=1, spec_lo=-q["w"],
+                       spec_hi=q["w"], spec_nbins=200, precision=1) for q in reqs]
+    t0 = time.perf_counter()
+    cal = served_burst(C, ctx, stream, list(zip(grids, specs)), read=lambda rid, sp: C.colt_read_result(ctx, rid, sp))
+    t_batch = time.perf_counter() - t0
+    rate = load * n_req / cal[1]
+    arr = np.cumsum(np.random.default_rng(4).exponential(1.0 / rate, n_req))
+    import torch
+    with ClockSampler(0) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        rids = []
+        for i in range(n_req):
+            while time.perf_counter() - t0 < arr[i]:
+                if rids:
+                    C.colt_poll(ctx, rids[-1])          # drive the scheduler between arrivals
+                time.sleep(0.0005)
+            rids.append(C.colt_submit(ctx, grids[i], specs[i]))
+        done = []
+        for rid, sp in zip(rids, specs):
+            C.colt_wait(ctx, rid, -1.0)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    for rid, sp in zip(rids, specs):
+        done.append((C.colt_poll(ctx, rid), C.colt_read_result(ctx, rid, sp)))
+        C.colt_release(ctx, rid)
+    ms = ev0.elapsed_time(ev1)
+    scat = sum(r["n_scat"] for _, r in done)
+    lat = [st["latency_ms"] for st, _ in done]
+    same = all(np.array_equal(a["spec"], b["spec"]) for a, (_, b) in zip(cal[2], done))
+    # the requests slowest in the mix, each solved alone (blocking launch): a
+    # lower bound of the longest single request's own time
+    slow = sorted(range(n_req), key=lambda i: -lat[i])[:5]
+    alone = {}
+    for i in slow:
+        r = C.colt_run(ctx, grids[i], specs[i])
+        alone[i] = r["kernel_ms"]
+    out = {"value": scat / (ms * 1e-3), "unit": UNIT,
+           "photons_per_s": sum(r["n_emitted"] for _, r in done) / (ms * 1e-3),
+           "served_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(max(lat)),
+                                 "n_requests": n_req,
+                                  "arrivals": f"Poisson, {rate:.3f} requests/s = {load:.2f} x the all-at-once "
+                                              f"throughput ({n_req} requests in {cal[1]:.1f} s)"},
+            "slowest_alone_ms": {str(i): alone[i] for i in slow},
+            "longest_alone_ms": float(max(alone.values())),
+            "batch_all_at_once": {"wall_s": cal[1], "latency_ms": {"p50": pct(cal[3], 50), "p99": pct(cal[3], 99)}},
+            "results_identical_across_mixes": same, "clocks": clk.summary(),
+            "config": {"workload": f"serving_mix_{n_req}req_64cubed", "precision": "mixed",
+                       "admission": "memory budget (90% of free HBM)"}}
+    for h in grids:
+        C.colt_destroy_grid(ctx, h)
+    return out
+
+
+def oracle_sample_cosmo(target_s=15.0, cores=0):
+    """The FP64 oracle, as it stands, on a bounded sample of the headline
+    workload: packets of the five sources (camera spectra, no images), the
+    grid derived once; the packet loop timed."""
+    import oracle as O
+    g, srcs, cams, cnb, label = octree_workload("cosmo")
+    cams0 = [S.Camera(c.direction, 0) for c in cams]
+    n = 2
+    while True:
+        specs = cosmo_specs(srcs, cams0, cnb, n, 10 ** 9)
+        t0 = time.perf_counter()
+        rs = O.run_many(g, specs, workers=5)
+        t = time.perf_counter() - t0
+        if t > target_s / 3 or n >= 1 << 12:
+            break
+        n *= 2
+    scat = sum(r["n_scat"] for r in rs)
+    return dict(value=scat / t, unit=UNIT, cores=os.cpu_count(), photons_per_s=5 * n / t, seconds=t, kind="oracle",
+                sample=f"{5 * n} packets ({n} per source) of {label}, three cameras' spectra (no images), five "
+                       f"sources run side by side on the host cores; the packet loop timed, grid derivation excluded "
+                       f"as on the GPU")
+
+
+def run_suite(args):
+    import torch
+    from paper_1409_4480_gb300 import colt as C
+    world, rank, local = _rank_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = C.colt_init(local, 0, stream.cuda_stream)
+    info = C.colt_device_info(ctx)
+    head = leg_cosmo(C, ctx, stream, args, info, world, rank)
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "photons_per_s": head["photons_per_s"], "served_latency_ms": head["latency"], "config": head["config"],
+            "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "e2e": head["e2e"],
+            "plain": head["plain"], "clocks": head["clocks"],
+            "counts": {"scatterings": head["scat"], "packets": head["packets"]}}
+    if rank == 0 and world == 1:
+        wl = {}
+        if not args.no_secondary:
+            wl["sphere128"] = leg_sphere(C, ctx, stream, args, info)
+            wl["halo"] = leg_halo(C, ctx, stream, args, info)
+            wl["serving"] = leg_serving(C, ctx, stream, args)
+        line["workloads"] = wl
+        if not args.no_cpu:
+            line["cpu_baseline"] = oracle_sample_cosmo(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    C.colt_finalize(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+
+
+def run_profile_case(args):
+    """One short launch of a workload with histories capped (ncu capture
+    driver): prints the launch's counters as JSON."""
+    from paper_1409_4480_gb300 import colt as C
+    ctx = C.colt_init(0)
+    name = args.profile_case
+    if name == "sphere128":
+        hs = [C.colt_create_grid(ctx, case_grid(t, v)) for t, v in cases()]
+        specs = [case_spec(i, 16384, 0, images=True) for i in range(9)]
+    else:
+        g, srcs, cams, cnb, label = octree_workload(name)
+        h = C.colt_create_grid(ctx, g)
+        if name == "cosmo":
+            # one source (a few GB on the device: the grid and one solve's image cubes)
+            specs = cosmo_specs(srcs[:1], cams, cnb, 16384, 0)
+        else:
+            pos, sig = srcs[0]
+            specs = [S.RunSpec(n_packets=65536, seed=300, src_pos=pos, src_sigma=sig, albedo=0.32, spec_units=1,
+                               spec_lo=-1000.0, spec_hi=1000.0, spec_nbins=200, cameras=cams, cam_units=1,
+                               cam_lo=-1000.0, cam_hi=1000.0, cam_nbins=cnb, precision=1)]
+        hs = [h] * len(specs)
+    for sp in specs:
+        sp.max_scatter = 2000
+    r = C.colt_run_batch(ctx, hs, specs, images=True, outputs=False)
+    print(json.dumps({"workload": name, "launches": 1, "kernel_ms": r[0]["kernel_ms"],
+                      "scatterings": sum(x["n_scat"] for x in r), "packets": sum(x["n_emitted"] for x in r),
+                      "cell_visits": r[0]["n_cell_visits"], "peel_visits": r[0]["n_peel_visits"],
+                      "peel_rays": r[0]["n_peel_rays"], "max_scatter": 2000,
+                      "kernel_source_sha256": kernel_source_hash()}), flush=True)
+    C.colt_finalize(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="colt", choices=["colt", "reference"])
-    ap.add_argument("--workload", default="sphere128",
-                    choices=["sphere128", "halo", "halo_diffuse", "cosmo", "serving", "tslab", "galaxies"])
+    ap.add_argument("--workload", default="suite",
+                    choices=["suite", "sphere128", "halo", "halo_diffuse", "cosmo", "serving", "tslab", "galaxies"])
     ap.add_argument("--core-skip", type=int, default=1, choices=[0, 1, 2],
                     help="octree and galaxy workloads: a tau_0 for x_crit (1 cell + non-local, 2 Jeans)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.75)
     ap.add_argument("--packets-per-case", type=int, default=None,
-                    help="packets per solve per step (default: 125000 for the sphere suite and --single-case; "
-                         "4096 halo / halo_diffuse / galaxies, 2048 cosmo, 20000 tslab)")
-    ap.add_argument("--ref-packets", type=int, default=2048)
+                    help="single-workload modes: packets per solve per step (default: 125000 for the sphere suite "
+                         "and --single-case; 4096 halo / halo_diffuse / galaxies, 2048 cosmo, 20000 tslab)")
+    ap.add_argument("--cosmo-packets", type=int, default=256, help="suite headline: packets per source per step")
+    ap.add_argument("--halo-packets", type=int, default=4096, help="suite: halo packets per step")
+    ap.add_argument("--halo-steps", type=int, default=8, help="suite: halo steps")
+    ap.add_argument("--sphere-steps", type=int, default=6, help="suite: sphere-suite steps")
+    ap.add_argument("--fp64-packets", type=int, default=100000, help="suite: packets of the plain FP64 solve")
+    ap.add_argument("--no-secondary", action="store_true", help="suite: the headline alone")
+    ap.add_argument("--ref-packets", type=int, default=16)
     ap.add_argument("--single-case", type=int, default=-1)
+    ap.add_argument("--profile-case", default=None, choices=["cosmo", "sphere128", "halo"])
     ap.add_argument("--max-scatter", type=int, default=0)
     ap.add_argument("--no-images", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    # algorithmic FP32 operations per unit (peel-off visit, flight cell visit, scattering)
-    ap.add_argument("--flops-peel", type=float, default=30.0)
-    ap.add_argument("--flops-cell", type=float, default=45.0)
-    ap.add_argument("--flops-scat", type=float, default=300.0)
     args = ap.parse_args()
     if args.packets_per_case is None:
         args.packets_per_case = {"halo": 4096, "halo_diffuse": 4096, "galaxies": 4096, "cosmo": 2048,
                                  "tslab": 20000}.get(args.workload, 125000)
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     elif args.single_case >= 0:
         run_single_case(args)
+    elif args.workload == "suite":
+        run_suite(args)
     elif args.workload in ("halo", "halo_diffuse", "cosmo"):
         run_octree(args)
     elif args.workload == "serving":

@@ -81,7 +81,7 @@ int colt_device_info(colt_ctx* ctx, int* sm_count, size_t* l2_bytes, int* cc_maj
  *   Octree: n_cells leaves; leaf i has refinement level leaf_level[i] (0 =
  *   root, at most 24) and integer coordinates leaf_ijk[3i..3i+2] at that
  *   level, i.e. it spans lo + ijk (hi-lo) 2^-level .. lo + (ijk+1) (hi-lo)
- *   2^-level.  The leaves must tile the box exactly, with fewer than 2^27 tree
+ *   2^-level.  The leaves must tile the box exactly, with fewer than 2^26 tree
  *   nodes (checked: COLT_EINVAL otherwise).  leaf_level / leaf_ijk are host
  *   arrays; the library builds a node table and per-leaf face neighbours
  *   (4 + 24 bytes per leaf beside the 32-byte record).
@@ -221,23 +221,40 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
                    colt_result* out);
 
 /* ------------------------------------------------------------ autotune -- */
-/* Launch configuration of the persistent transport kernel: a register
- * variant (0: the compiler's allocation; 1 / 2: registers capped so that four
- * / three 256-thread CTAs fit on an SM, FP32 only) and the resident CTAs per
- * SM (0 = as many as fit).  The library default is {0, 0}. */
+/* Launch configuration of the persistent transport kernel:
+ *   variant         register variant (0: the compiler's allocation; 1 / 2:
+ *                   registers capped so that four / three 256-thread CTAs fit
+ *                   on an SM, FP32 only)
+ *   blocks_per_sm   resident CTAs per SM (0 = as many as fit)
+ *   warps_per_block 8 (4 and 16 also exist for the FP32 variant 0; 0 = 8)
+ *   refill_min      a warp takes new packets once this many of its 32 lanes
+ *                   are idle, or when all are (1 = every round; 0 = 1)
+ * Each lane carries one packet (32 packets per warp).  The library default is
+ * {0, 0, 0, 8, 1}.  Results never depend on the configuration (packets are
+ * keyed by id), up to the summation order of the peel-off tallies. */
 typedef struct {
   int variant;
   int blocks_per_sm;
   double scatterings_per_s;  /* measured by colt_autotune */
+  int warps_per_block;
+  int refill_min;
 } colt_launch_config;
 
-/* Run the solve (grid, *params) -- at most 2^20 packets, no images, the same
- * packet ids each time -- once under every configuration the build offers,
- * keep the fastest for params->precision and the grid's kind (every later
- * launch of that pair with blocks_per_sm = 0 uses it, served launches
- * included) and report it in *out (may be NULL).  Blocking; costs one solve
- * per configuration (six for FP32, two for FP64). */
+/* Tune the launch configuration on the solve (grid, *params) -- at most 2^20
+ * packets, no images, the same packet ids each time -- by a coordinate search:
+ * every register variant x resident CTAs per SM, then warps per CTA, then the
+ * refill threshold (1, 4, 12), one solve per configuration.  The fastest is
+ * kept for params->precision and the grid's kind (every later launch of that
+ * pair with blocks_per_sm = 0 uses it, served launches included) and reported
+ * in *out (may be NULL).  Blocking; about eleven solves for FP32, four for
+ * FP64. */
 int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out);
+
+/* Set the launch configuration used for `precision` (COLT_PLAIN / COLT_MIXED)
+ * and grid kind `kind` (COLT_CARTESIAN / COLT_OCTREE) without tuning;
+ * COLT_EINVAL for a variant, block size or refill threshold (1..32) the build
+ * does not offer.  blocks_per_sm = 0 means as many CTAs as fit. */
+int colt_set_launch_config(colt_ctx* ctx, int precision, int kind, const colt_launch_config* cfg);
 
 /* Same solve with HOST input fields: builds a temporary grid from desc, runs,
  * copies results back and frees the grid (one call for an end-to-end user). */
@@ -245,14 +262,16 @@ int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params*
 
 /* ------------------------------------------------------------- serving -- */
 /* Continuous batching.  colt_submit enqueues a solve (non-blocking); requests
- * are admitted as memory (mem_budget_bytes) and batch slots free up, and the
- * packets of all admitted requests share persistent launches (up to three in
- * flight; each launch holds requests of one precision and one grid kind,
- * longest expected histories first, a request passed over four times first).  Returns
- * COLT_EAGAIN when the request cannot be queued now (queue full).  The grid
- * must stay alive until the request is released.  Results of a request are
- * identical to colt_run of the same (grid, params) up to floating-point
- * summation order of the peel-off tallies. */
+ * are admitted as memory (mem_budget_bytes) allows, and the packets of all
+ * admitted requests share persistent launches (up to six in flight, each of
+ * at most 256 requests and 2^20 packets, one precision and one grid kind;
+ * longest expected histories first, a request passed over four times first).
+ * A request is done as soon as all its own packets have finished, whatever
+ * else its launches still run.  Returns COLT_EAGAIN when the request cannot
+ * be queued now (queue full).  The grid must stay alive until the request is
+ * released.  Results of a request are identical to colt_run of the same
+ * (grid, params) up to floating-point summation order of the peel-off
+ * tallies. */
 typedef struct {
   int done;                 /* 1 when all packets are finished                   */
   int admitted;

@@ -30,7 +30,8 @@ COLT_SOURCE_POINT, COLT_SOURCE_CELLS = 0, 1
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
            "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
            "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
-           "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity", "colt_cancel"]
+           "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity", "colt_cancel",
+           "colt_set_launch_config"]
 
 _LIB = None
 
@@ -82,7 +83,8 @@ class Stats(C.Structure):
 
 
 class LaunchConfig(C.Structure):
-    _fields_ = [("variant", C.c_int), ("blocks_per_sm", C.c_int), ("scatterings_per_s", C.c_double)]
+    _fields_ = [("variant", C.c_int), ("blocks_per_sm", C.c_int), ("scatterings_per_s", C.c_double),
+                ("warps_per_block", C.c_int), ("refill_min", C.c_int)]
 
 
 class ScatterIO(C.Structure):
@@ -131,6 +133,7 @@ def lib():
             "colt_read_result": (I, [P, U64, P]),
             "colt_release": (I, [P, U64]),
             "colt_cancel": (I, [P, U64]),
+            "colt_set_launch_config": (I, [P, I, I, P]),
             "colt_voigt": (I, [P, P, P, P, SZ, I, I]),
             "colt_scatter": (I, [P, P, SZ, U64, I]),
             "colt_run_noalloc": (I, [I, P, P, P, P]),
@@ -368,7 +371,15 @@ def colt_autotune(ctx, grid: int, spec) -> dict:
     p, cams = run_params(spec, False)
     out = LaunchConfig()
     _check(ctx, lib().colt_autotune(ctx, C.c_uint64(grid), C.byref(p), C.byref(out)))
-    return dict(variant=out.variant, blocks_per_sm=out.blocks_per_sm, scatterings_per_s=out.scatterings_per_s)
+    return dict(variant=out.variant, blocks_per_sm=out.blocks_per_sm, scatterings_per_s=out.scatterings_per_s,
+                warps_per_block=out.warps_per_block, refill_min=out.refill_min)
+
+
+def colt_set_launch_config(ctx, precision: int, kind: int, variant: int = 0, blocks_per_sm: int = 0,
+                           warps_per_block: int = 8, refill_min: int = 1):
+    c = LaunchConfig(variant=variant, blocks_per_sm=blocks_per_sm, scatterings_per_s=0.0,
+                     warps_per_block=warps_per_block, refill_min=refill_min)
+    _check(ctx, lib().colt_set_launch_config(ctx, int(precision), int(kind), C.byref(c)))
 
 
 def colt_submit(ctx, grid: int, spec, images: bool = True) -> int:

@@ -8,7 +8,10 @@
 // keep several launches in flight: the GPU's block scheduler hands SMs freed
 // by one launch's finished CTAs to the next launch, so a launch's tail of
 // long histories overlaps new work.  Slot 0 runs on the context stream and
-// also serves the blocking calls.
+// also serves the blocking calls.  Every launch counts each job's finished
+// packets in mapped host memory, so a served request completes with its own
+// packets; tally set-up, grid building and result copies run on an
+// auxiliary stream, never behind a launch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,7 +35,7 @@ using namespace colt;
 namespace {
 
 constexpr int kMaxJobs = 256;                  // solves per persistent launch
-constexpr int kSlots = 3;                      // launches in flight (serving)
+constexpr int kSlots = 6;                      // launches in flight (serving)
 constexpr uint64_t kStepPackets = 1ull << 20;  // packet budget of one serving launch
 constexpr int kWorkWords = 8;                  // work counter + launch counters (+ phase clocks)
 constexpr int kMaxPassed = 4;                  // launches a ready request may be passed over
@@ -73,6 +76,8 @@ struct LaunchBuf {
   size_t bytes = 0;
   unsigned long long* work = nullptr;   // device: next counter + launch counters, then job_max
   unsigned long long* jmax_h = nullptr; // pinned copy of job_max after the launch
+  unsigned long long* jdone_h = nullptr; // pinned, mapped: packets of each job finished (written by the kernel)
+  unsigned long long* jdone_d = nullptr; // its device address
   int* error = nullptr;
   LaunchDev* hdr_h() { return reinterpret_cast<LaunchDev*>(host); }
   unsigned long long* end_h() { return reinterpret_cast<unsigned long long*>(host + 256); }
@@ -88,6 +93,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   bool in_flight = false;
   std::vector<std::pair<uint64_t, uint64_t>> jobs;  // (request id, packets)
+  std::vector<char> credited;                       // job's packets already counted to its request
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][grid kind]
   int graph_cfg[2][2] = {{-1, -1}, {-1, -1}};                               // launch configuration captured
 };
@@ -143,6 +149,9 @@ struct colt_ctx {
   std::map<uint64_t, std::unique_ptr<Req>> reqs;
   std::deque<uint64_t> queue;           // queued request ids (FIFO)
   Slot slots[kSlots];
+  // library-internal stream for tally set-up, grid building and result
+  // copies, so that none of them queues behind a launch on the context stream
+  cudaStream_t aux = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_alloc = nullptr;
   uint64_t launches = 0;                // transport kernel launches issued
   // completion signal of serving launches: a host function enqueued behind
@@ -151,7 +160,7 @@ struct colt_ctx {
   std::condition_variable cv;
   uint64_t done_seq = 0;
   // launch configuration per [precision][grid kind] (colt_autotune)
-  colt_launch_config cfg[2][2] = {{{0, 0, 0.0}, {0, 0, 0.0}}, {{0, 0, 0.0}, {0, 0, 0.0}}};
+  colt_launch_config cfg[2][2] = {{{0, 0, 0.0, 8, 1}, {0, 0, 0.0, 8, 1}}, {{0, 0, 0.0, 8, 1}, {0, 0, 0.0, 8, 1}}};
 };
 
 namespace {
@@ -195,9 +204,9 @@ size_t tally_bytes(const colt_run_params* p, bool per_packet) {
 // Allocate and zero one solve's tallies (stream-ordered pool on the context stream).
 int alloc_tally(colt_ctx* ctx, const colt_run_params* p, bool per_packet, Tally* t) {
   t->bytes = tally_bytes(p, per_packet) + 256;
-  t->stream = ctx->stream;
-  CU(cudaMallocAsync(&t->block, t->bytes, ctx->stream));
-  CU(cudaMemsetAsync(t->block, 0, t->bytes, ctx->stream));
+  t->stream = ctx->aux;
+  CU(cudaMallocAsync(&t->block, t->bytes, ctx->aux));
+  CU(cudaMemsetAsync(t->block, 0, t->bytes, ctx->aux));
   unsigned char* q = static_cast<unsigned char*>(t->block);
   auto take = [&](size_t n) {
     unsigned char* r = q;
@@ -256,6 +265,8 @@ int ensure_slot(colt_ctx* ctx, int si) {
   CU(cudaMalloc(&lb.dev, lb.bytes));
   CU(cudaMalloc(&lb.work, sizeof(unsigned long long) * (kWorkWords + kMaxJobs)));
   CU(cudaMallocHost(&lb.jmax_h, sizeof(unsigned long long) * kMaxJobs));
+  CU(cudaHostAlloc(&lb.jdone_h, sizeof(unsigned long long) * kMaxJobs, cudaHostAllocMapped));
+  std::memset(lb.jdone_h, 0, sizeof(unsigned long long) * kMaxJobs);
   CU(cudaMalloc(&lb.error, sizeof(int)));
   CU(cudaMemset(lb.error, 0, sizeof(int)));
   std::memset(lb.host, 0, lb.bytes);
@@ -266,6 +277,8 @@ int ensure_slot(colt_ctx* ctx, int si) {
   h->counters = lb.work + 1;
   h->error = lb.error;
   h->job_max = lb.work + kWorkWords;
+  // finished-packet counts per job (set per launch: serving launches only)
+  CU(cudaHostGetDevicePointer(reinterpret_cast<void**>(&lb.jdone_d), lb.jdone_h, 0));
   return COLT_OK;
 }
 
@@ -278,17 +291,22 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
   const int gi = precision == COLT_PLAIN ? 0 : 1;
   const int gk = kind == COLT_OCTREE ? 1 : 0;
   const colt_launch_config& cfg = ctx->cfg[gi][gk];
+  const int warps = cfg.warps_per_block > 0 && transport_has_warps(precision, cfg.variant, cfg.warps_per_block)
+                        ? cfg.warps_per_block : 8;
+  lb.hdr_h()->refill_min = std::max(1, cfg.refill_min);
+  // the slot's previous launch has ended: nothing writes the counts now
+  std::memset(lb.jdone_h, 0, sizeof(unsigned long long) * kMaxJobs);
   ++ctx->launches;
   if (blocks_per_sm > 0) {
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
     CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
     CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant, blocks_per_sm,
-                        ctx->sm_count, sl.stream, extras));
+                        ctx->sm_count, sl.stream, extras, warps));
     CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
   }
-  const int code = cfg.variant * 64 + cfg.blocks_per_sm + (extras ? 4096 : 0);
+  const int code = cfg.variant * 64 + cfg.blocks_per_sm + (extras ? 4096 : 0) + warps * 8192;
   if (sl.graph[gi][gk] && sl.graph_cfg[gi][gk] != code) {
     cudaGraphExecDestroy(sl.graph[gi][gk]);
     sl.graph[gi][gk] = nullptr;
@@ -299,7 +317,7 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream);
     cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
     cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant,
-                                      cfg.blocks_per_sm, ctx->sm_count, sl.stream, extras);
+                                      cfg.blocks_per_sm, ctx->sm_count, sl.stream, extras, warps);
     cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                     cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
@@ -331,25 +349,25 @@ int check_device_error(colt_ctx* ctx, int si) {
 // Copy a solve's tallies into a caller's colt_result.
 int copy_result(colt_ctx* ctx, const colt_run_params* p, const Tally& t, colt_result* out, bool per_packet) {
   unsigned long long cnt[kNumCounters];
-  CU(cudaMemcpyAsync(cnt, t.counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(cnt, t.counters, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->aux));
   if (out->spec)
-    CU(cudaMemcpyAsync(out->spec, t.spec, sizeof(uint64_t) * p->spec_nbins, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(out->spec, t.spec, sizeof(uint64_t) * p->spec_nbins, cudaMemcpyDeviceToHost, ctx->aux));
   if (p->n_cam > 0) {
     const size_t ns = (size_t)p->n_cam * p->cam_nbins;
-    if (out->cam_spec) CU(cudaMemcpyAsync(out->cam_spec, t.cam_spec, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
-    if (out->cam_spec2) CU(cudaMemcpyAsync(out->cam_spec2, t.cam_spec2, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->cam_spec) CU(cudaMemcpyAsync(out->cam_spec, t.cam_spec, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->aux));
+    if (out->cam_spec2) CU(cudaMemcpyAsync(out->cam_spec2, t.cam_spec2, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->aux));
     if (out->cam_image && t.cam_image) {
       size_t img = 0;
       for (int i = 0; i < p->n_cam; ++i) img += (size_t)p->cams[i].npix * p->cams[i].npix * p->cam_nbins;
-      CU(cudaMemcpyAsync(out->cam_image, t.cam_image, sizeof(double) * img, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaMemcpyAsync(out->cam_image, t.cam_image, sizeof(double) * img, cudaMemcpyDeviceToHost, ctx->aux));
     }
   }
   if (per_packet) {
-    if (out->pk_status) CU(cudaMemcpyAsync(out->pk_status, t.pk_status, sizeof(int32_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
-    if (out->pk_nscat) CU(cudaMemcpyAsync(out->pk_nscat, t.pk_nscat, sizeof(uint64_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
-    if (out->pk_freq) CU(cudaMemcpyAsync(out->pk_freq, t.pk_freq, sizeof(double) * p->n_packets, cudaMemcpyDeviceToHost, ctx->stream));
+    if (out->pk_status) CU(cudaMemcpyAsync(out->pk_status, t.pk_status, sizeof(int32_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->aux));
+    if (out->pk_nscat) CU(cudaMemcpyAsync(out->pk_nscat, t.pk_nscat, sizeof(uint64_t) * p->n_packets, cudaMemcpyDeviceToHost, ctx->aux));
+    if (out->pk_freq) CU(cudaMemcpyAsync(out->pk_freq, t.pk_freq, sizeof(double) * p->n_packets, cudaMemcpyDeviceToHost, ctx->aux));
   }
-  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaStreamSynchronize(ctx->aux));
   out->n_emitted = cnt[kEmitted];
   out->n_escaped = cnt[kEscaped];
   out->n_absorbed = cnt[kAbsorbed];
@@ -369,6 +387,7 @@ constexpr int32_t kUnset = INT32_MIN;
 int build_octree_tables(colt_ctx* ctx, int64_t n, const uint8_t* lev, const uint32_t* ijk,
                         std::vector<int32_t>* node_out, std::vector<uint32_t>* nbr_out, int* max_level) {
   std::vector<int32_t>& node = *node_out;
+  if (n > (int64_t)kNodeMask) return fail(ctx, COLT_EINVAL, "octree has too many leaves");
   node.assign(1, kUnset);
   int maxl = 0;
   for (int64_t l = 0; l < n; ++l) {
@@ -414,7 +433,8 @@ int build_octree_tables(colt_ctx* ctx, int64_t n, const uint8_t* lev, const uint
           for (int a = 0; a < 3; ++a) cidx |= (int)((adj[a] >> (L - t)) & 1) << a;
           v = (size_t)node[v] + cidx;
         }
-        nbr[6 * l + f] = (uint32_t)v | ((uint32_t)t << 27);
+        nbr[6 * l + f] = node[v] < 0 ? ((uint32_t)(-1 - node[v]) | kLeafFlag | ((uint32_t)t << 27))
+                                     : ((uint32_t)v | ((uint32_t)t << 27));
       }
     }
   };
@@ -453,13 +473,13 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
     if (!src[i]) { f[i] = nullptr; continue; }
     if (d->fields_mem == COLT_MEM_DEVICE) {
       hf[i].resize(n);
-      CU(cudaMemcpyAsync(hf[i].data(), src[i], sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaMemcpyAsync(hf[i].data(), src[i], sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->aux));
       f[i] = hf[i].data();
     } else {
       f[i] = src[i];
     }
   }
-  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaStreamSynchronize(ctx->aux));
   std::vector<int32_t> node;
   std::vector<uint32_t> nbr;
   int max_level = 0;
@@ -498,36 +518,36 @@ int build_grid(colt_ctx* ctx, const colt_grid_desc* d, GridObj* g) {
   G.n_cells = n;
   G.max_level = max_level;
   CU(cudaMalloc(&g->rec, sizeof(float4) * 2 * (size_t)n));
-  CU(cudaMemcpyAsync(g->rec, rec.data(), sizeof(float4) * 2 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(g->rec, rec.data(), sizeof(float4) * 2 * (size_t)n, cudaMemcpyHostToDevice, ctx->aux));
   G.rec = g->rec;
   if (oct) {
     CU(cudaMalloc(&g->node, sizeof(int32_t) * node.size()));
     CU(cudaMalloc(&g->nbr, sizeof(uint32_t) * nbr.size()));
-    CU(cudaMemcpyAsync(g->node, node.data(), sizeof(int32_t) * node.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(g->nbr, nbr.data(), sizeof(uint32_t) * nbr.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(g->node, node.data(), sizeof(int32_t) * node.size(), cudaMemcpyHostToDevice, ctx->aux));
+    CU(cudaMemcpyAsync(g->nbr, nbr.data(), sizeof(uint32_t) * nbr.size(), cudaMemcpyHostToDevice, ctx->aux));
     G.node = g->node;
     G.nbr = g->nbr;
   }
   // non-local a tau (Eq. atauNL), once per grid
   float* dn = nullptr;
-  CU(cudaMallocAsync(&dn, sizeof(float) * n, ctx->stream));
-  CU(cudaMemcpyAsync(dn, f[0], sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMallocAsync(&dn, sizeof(float) * n, ctx->aux));
+  CU(cudaMemcpyAsync(dn, f[0], sizeof(float) * n, cudaMemcpyHostToDevice, ctx->aux));
   cudaError_t e = cudaSuccess;
   if (oct) {
     uint8_t* dlev = nullptr;
     uint32_t* dijk = nullptr;
-    CU(cudaMallocAsync(&dlev, (size_t)n, ctx->stream));
-    CU(cudaMallocAsync(&dijk, sizeof(uint32_t) * 3 * (size_t)n, ctx->stream));
-    CU(cudaMemcpyAsync(dlev, d->leaf_level, (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(dijk, d->leaf_ijk, sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
-    e = launch_atau_nl_oct(G, dn, dlev, dijk, d->f_nl, g->rec, ctx->stream);
-    cudaFreeAsync(dlev, ctx->stream);
-    cudaFreeAsync(dijk, ctx->stream);
+    CU(cudaMallocAsync(&dlev, (size_t)n, ctx->aux));
+    CU(cudaMallocAsync(&dijk, sizeof(uint32_t) * 3 * (size_t)n, ctx->aux));
+    CU(cudaMemcpyAsync(dlev, d->leaf_level, (size_t)n, cudaMemcpyHostToDevice, ctx->aux));
+    CU(cudaMemcpyAsync(dijk, d->leaf_ijk, sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->aux));
+    e = launch_atau_nl_oct(G, dn, dlev, dijk, d->f_nl, g->rec, ctx->aux);
+    cudaFreeAsync(dlev, ctx->aux);
+    cudaFreeAsync(dijk, ctx->aux);
   } else {
-    e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->stream);
+    e = launch_atau_nl(G, dn, d->f_nl, g->rec, ctx->aux);
   }
-  cudaFreeAsync(dn, ctx->stream);
-  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(dn, ctx->aux);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->aux);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "atau_nl kernel");
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "atau_nl sync");
   g->bytes = bytes;
@@ -555,24 +575,42 @@ void learn_cost(colt_ctx* ctx, colt_grid grid, uint64_t longest) {
   g->second.measured = true;
 }
 
-// A slot's launch finished: account its packets to its requests.
-int complete_slot(colt_ctx* ctx, int si) {
+// Count the packets of a slot's jobs to their requests: every job once the
+// launch has ended (all), else the jobs whose packets have all finished
+// (the kernel bumps the job's count in mapped host memory after a fence, so
+// the job's tallies are complete when the count is).  A request is done when
+// all its packets are.
+void credit_jobs(colt_ctx* ctx, int si, bool all) {
   Slot& sl = ctx->slots[si];
-  sl.in_flight = false;
+  const volatile unsigned long long* done = sl.lb.jdone_h;
   const double t = now_ms();
   for (size_t j = 0; j < sl.jobs.size(); ++j) {
+    if (sl.credited[j]) continue;
     const auto& jp = sl.jobs[j];
+    if (!all && done[j] < jp.second) continue;
+    sl.credited[j] = 1;
     auto it = ctx->reqs.find(jp.first);
     if (it == ctx->reqs.end()) continue;
     Req& r = *it->second;
-    learn_cost(ctx, r.grid, sl.lb.jmax_h[j]);
     r.done_packets += jp.second;
     if (r.done_packets >= r.target && r.state == kAdmitted) {
       r.state = kDone;
       r.t_done = t;
     }
   }
+}
+
+// A slot's launch finished: account its packets to its requests.
+int complete_slot(colt_ctx* ctx, int si) {
+  Slot& sl = ctx->slots[si];
+  sl.in_flight = false;
+  for (size_t j = 0; j < sl.jobs.size(); ++j) {
+    auto it = ctx->reqs.find(sl.jobs[j].first);
+    if (it != ctx->reqs.end()) learn_cost(ctx, it->second->grid, sl.lb.jmax_h[j]);
+  }
+  credit_jobs(ctx, si, true);
   sl.jobs.clear();
+  sl.credited.clear();
   return check_device_error(ctx, si);
 }
 
@@ -606,7 +644,7 @@ int serve_admit(colt_ctx* ctx) {
     ctx->queue.pop_front();
     ++admitted;
   }
-  if (admitted) CU(cudaEventRecord(ctx->ev_alloc, ctx->stream));
+  if (admitted) CU(cudaEventRecord(ctx->ev_alloc, ctx->aux));
   return admitted;
 }
 
@@ -664,6 +702,7 @@ int serve_launch(colt_ctx* ctx, int si) {
   int nj = 0;
   bool extras = false;
   sl.jobs.clear();
+  sl.credited.clear();
   for (size_t i = 0; i < sel.size() && left > 0; ++i) {
     Req* r = sel[i];
     const uint64_t rem = r->target - r->next_local;
@@ -681,6 +720,7 @@ int serve_launch(colt_ctx* ctx, int si) {
     lb.end_h()[nj] = total;
     r->next_local += take;
     sl.jobs.push_back({r->id, take});
+    sl.credited.push_back(0);
     left = left > take ? left - take : 0;
     ++nj;
   }
@@ -693,6 +733,8 @@ int serve_launch(colt_ctx* ctx, int si) {
   LaunchDev* h = lb.hdr_h();
   h->n_jobs = nj;
   h->total = total;
+  // served requests complete with their own packets: count them per job
+  h->job_done = lb.jdone_d;
   // tallies were allocated and zeroed on the context stream
   CU(cudaStreamWaitEvent(sl.stream, ctx->ev_alloc, 0));
   rc = enqueue_launch(ctx, si, prec, kind, 0, extras);
@@ -709,7 +751,10 @@ int serve_pump(colt_ctx* ctx) {
     Slot& sl = ctx->slots[si];
     if (!sl.in_flight) continue;
     cudaError_t q = cudaEventQuery(sl.done);
-    if (q == cudaErrorNotReady) continue;
+    if (q == cudaErrorNotReady) {
+      credit_jobs(ctx, si, false);
+      continue;
+    }
     if (q != cudaSuccess) return cuda_fail(ctx, q, "serving launch");
     int rc = complete_slot(ctx, si);
     if (rc) return rc;
@@ -759,6 +804,11 @@ int colt_init(colt_ctx** out, int device, size_t mem_budget_bytes, void* cuda_st
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return COLT_ECUDA;
+  }
   cudaEventCreate(&ctx->ev0);
   cudaEventCreate(&ctx->ev1);
   cudaEventCreateWithFlags(&ctx->ev_alloc, cudaEventDisableTiming);
@@ -774,8 +824,10 @@ void colt_finalize(colt_ctx* ctx) {
     for (auto& sl : ctx->slots)
       if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->aux);
     for (auto& kv : ctx->reqs) free_tally(&kv.second->tally);
     for (auto& kv : ctx->grids) free_grid(kv.second);
+    cudaStreamSynchronize(ctx->aux);
     cudaStreamSynchronize(ctx->stream);
     for (auto& sl : ctx->slots) {
       for (auto& gp : sl.graph)
@@ -784,6 +836,7 @@ void colt_finalize(colt_ctx* ctx) {
       if (sl.lb.dev) cudaFree(sl.lb.dev);
       if (sl.lb.work) cudaFree(sl.lb.work);
       if (sl.lb.jmax_h) cudaFreeHost(sl.lb.jmax_h);
+      if (sl.lb.jdone_h) cudaFreeHost(sl.lb.jdone_h);
       if (sl.lb.error) cudaFree(sl.lb.error);
       if (sl.done) cudaEventDestroy(sl.done);
       if (sl.own_stream) cudaStreamDestroy(sl.stream);
@@ -791,6 +844,7 @@ void colt_finalize(colt_ctx* ctx) {
     cudaEventDestroy(ctx->ev0);
     cudaEventDestroy(ctx->ev1);
     cudaEventDestroy(ctx->ev_alloc);
+    cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;
@@ -814,7 +868,7 @@ int colt_create_grid(colt_ctx* ctx, const colt_grid_desc* desc, colt_grid* out) 
   GridObj g;
   int rc = build_grid(ctx, desc, &g);
   if (rc) {
-    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->aux);
     free_grid(g);
     return rc;
   }
@@ -833,7 +887,7 @@ int colt_destroy_grid(colt_ctx* ctx, colt_grid grid) {
   for (auto& kv : ctx->reqs)
     if (kv.second->grid == grid && kv.second->state != kDone)
       return fail(ctx, COLT_EINVAL, "grid is in use by an unfinished request");
-  cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->aux);
   free_grid(it->second);
   ctx->used -= it->second.bytes;
   ctx->grids.erase(it);
@@ -846,8 +900,8 @@ int colt_read_cells(colt_ctx* ctx, colt_grid grid, float* out, size_t n_floats) 
   auto it = ctx->grids.find(grid);
   if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
   if (n_floats != 8 * (size_t)it->second.dev.n_cells) return fail(ctx, COLT_EINVAL, "n_floats must be 8 * n_cells");
-  CU(cudaMemcpyAsync(out, it->second.rec, sizeof(float) * n_floats, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaMemcpyAsync(out, it->second.rec, sizeof(float) * n_floats, cudaMemcpyDeviceToHost, ctx->aux));
+  CU(cudaStreamSynchronize(ctx->aux));
   return COLT_OK;
 }
 
@@ -868,8 +922,8 @@ int colt_set_cell_luminosity(colt_ctx* ctx, colt_grid grid, const double* lum, i
   const double* L = lum;
   if (mem == COLT_MEM_DEVICE) {
     hl.resize(n);
-    CU(cudaMemcpyAsync(hl.data(), lum, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(hl.data(), lum, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->aux));
+    CU(cudaStreamSynchronize(ctx->aux));
     L = hl.data();
   }
   // integer weights w_c = floor(2^s lum_c / max lum), s = 63 - ceil(log2(n + 1)):
@@ -910,11 +964,11 @@ int colt_set_cell_luminosity(colt_ctx* ctx, colt_grid grid, const double* lum, i
   };
   cudaError_t e = cudaMalloc(&cum_d, sizeof(unsigned long long) * (size_t)n);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(cum_d, cum.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+    e = cudaMemcpyAsync(cum_d, cum.data(), sizeof(unsigned long long) * (size_t)n, cudaMemcpyHostToDevice, ctx->aux);
   if (e == cudaSuccess && oct) e = cudaMalloc(&loc_d, sizeof(uint32_t) * 3 * (size_t)n);
   if (e == cudaSuccess && oct)
-    e = cudaMemcpyAsync(loc_d, loc.data(), sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    e = cudaMemcpyAsync(loc_d, loc.data(), sizeof(uint32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->aux);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux);
   if (e != cudaSuccess) {
     release_new();
     return cuda_fail(ctx, e, "luminosity table");
@@ -988,8 +1042,12 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
   LaunchDev* h = lb.hdr_h();
   h->n_jobs = n;
   h->total = total;
+  h->job_done = nullptr;     // a blocking run completes with its launch
   unsigned long long lcnt[kNumLaunchCounters] = {0, 0, 0};
   float ms = 0;
+  // the tallies were set up on the auxiliary stream
+  CU(cudaEventRecord(ctx->ev_alloc, ctx->aux));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_alloc, 0));
   if (total > 0) {
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
     rc = enqueue_launch(ctx, 0, prec, kind, params[0].blocks_per_sm, extras);
@@ -1043,31 +1101,73 @@ int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, 
   q.n_packets = std::min<uint64_t>(q.n_packets, 1ull << 20);
   std::vector<uint64_t> spec(q.spec_nbins);
   std::vector<double> cs((size_t)std::max(1, q.n_cam) * q.cam_nbins), cs2(cs.size());
-  colt_launch_config best{0, 0, -1.0};
+  auto time_cfg = [&](const colt_launch_config& c, double* rate) -> int {
+    ctx->cfg[gi][gk] = c;
+    colt_result r{};
+    r.spec = spec.data();
+    if (q.n_cam > 0) {
+      r.cam_spec = cs.data();
+      r.cam_spec2 = cs2.data();
+    }
+    const int e = colt_run_batch(ctx, 1, &grid, &q, &r);
+    if (e) {
+      ctx->cfg[gi][gk] = colt_launch_config{0, 0, 0.0, 8, 1};
+      return e;
+    }
+    *rate = r.kernel_ms > 0 ? (double)r.n_scat / (r.kernel_ms * 1e-3) : 0.0;
+    return COLT_OK;
+  };
+  colt_launch_config best{0, 0, -1.0, 8, 1};
+  // 1. register variant x resident CTAs per SM (8 warps, refill every round)
   for (int v = 0; v < transport_variants(prec); ++v) {
-    const int occ = transport_occupancy(prec, kind, v);
+    const int occ = transport_occupancy(prec, kind, v, 8);
     for (int b = occ; b >= std::max(1, occ - 1); --b) {
-      ctx->cfg[gi][gk] = colt_launch_config{v, b, 0.0};
       double rate = 0.0;
-      for (int rep = 0; rep < 1; ++rep) {
-        colt_result r{};
-        r.spec = spec.data();
-        if (q.n_cam > 0) {
-          r.cam_spec = cs.data();
-          r.cam_spec2 = cs2.data();
-        }
-        rc = colt_run_batch(ctx, 1, &grid, &q, &r);
-        if (rc) {
-          ctx->cfg[gi][gk] = colt_launch_config{0, 0, 0.0};
-          return rc;
-        }
-        rate = r.kernel_ms > 0 ? (double)r.n_scat / (r.kernel_ms * 1e-3) : 0.0;
-      }
-      if (rate > best.scatterings_per_s) best = colt_launch_config{v, b, rate};
+      rc = time_cfg(colt_launch_config{v, b, 0.0, 8, 1}, &rate);
+      if (rc) return rc;
+      if (rate > best.scatterings_per_s) best = colt_launch_config{v, b, rate, 8, 1};
+    }
+  }
+  // 2. warps per CTA, at the most CTAs per SM that fit
+  for (int w : {4, 16}) {
+    if (!transport_has_warps(prec, best.variant, w)) continue;
+    const int occ = transport_occupancy(prec, kind, best.variant, w);
+    double rate = 0.0;
+    rc = time_cfg(colt_launch_config{best.variant, occ, 0.0, w, 1}, &rate);
+    if (rc) return rc;
+    if (rate > best.scatterings_per_s) best = colt_launch_config{best.variant, occ, rate, w, 1};
+  }
+  // 3. refill threshold
+  for (int m : {4, 12}) {
+    double rate = 0.0;
+    colt_launch_config c = best;
+    c.refill_min = m;
+    rc = time_cfg(c, &rate);
+    if (rc) return rc;
+    if (rate > best.scatterings_per_s) {
+      best = c;
+      best.scatterings_per_s = rate;
     }
   }
   ctx->cfg[gi][gk] = best;
   if (out) *out = best;
+  return COLT_OK;
+}
+
+int colt_set_launch_config(colt_ctx* ctx, int precision, int kind, const colt_launch_config* cfg) {
+  if (!ctx || !cfg) return COLT_EINVAL;
+  if (precision != COLT_PLAIN && precision != COLT_MIXED) return fail(ctx, COLT_EINVAL, "bad precision");
+  if (kind != COLT_CARTESIAN && kind != COLT_OCTREE) return fail(ctx, COLT_EINVAL, "bad grid kind");
+  const int w = cfg->warps_per_block > 0 ? cfg->warps_per_block : 8;
+  if (cfg->variant < 0 || cfg->variant >= transport_variants(precision) || !transport_has_warps(precision, cfg->variant, w))
+    return fail(ctx, COLT_EINVAL, "this build has no such kernel variant / block size");
+  if (cfg->blocks_per_sm < 0 || cfg->refill_min < 0 || cfg->refill_min > 32)
+    return fail(ctx, COLT_EINVAL, "bad blocks_per_sm or refill_min");
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  colt_launch_config c = *cfg;
+  c.warps_per_block = w;
+  c.refill_min = std::max(1, cfg->refill_min);
+  ctx->cfg[precision == COLT_PLAIN ? 0 : 1][kind == COLT_OCTREE ? 1 : 0] = c;
   return COLT_OK;
 }
 
@@ -1179,7 +1279,9 @@ int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms) {
       if (rc) return rc;
       if (done) return COLT_OK;
     }
-    double wait_ms = 20.0;   // re-poll at least this often (a queued request may wait on memory)
+    // re-poll at least this often: a request can finish inside a running
+    // launch (its own packets done), and a queued one may wait on memory
+    double wait_ms = 1.0;
     if (timeout_ms >= 0) {
       const double left = timeout_ms - (now_ms() - t0);
       if (left <= 0) return fail(ctx, COLT_ETIMEOUT, "colt_wait timed out");
@@ -1229,16 +1331,16 @@ int colt_read_spectrum(colt_ctx* ctx, colt_req req, int camera, double* buf, siz
     if (nbins != (size_t)r.p.spec_nbins) return fail(ctx, COLT_EINVAL, "nbins mismatch");
     std::vector<uint64_t> h(nbins, 0);
     if (r.tally.block) {
-      CU(cudaMemcpyAsync(h.data(), r.tally.spec, sizeof(uint64_t) * nbins, cudaMemcpyDeviceToHost, ctx->stream));
-      CU(cudaStreamSynchronize(ctx->stream));
+      CU(cudaMemcpyAsync(h.data(), r.tally.spec, sizeof(uint64_t) * nbins, cudaMemcpyDeviceToHost, ctx->aux));
+      CU(cudaStreamSynchronize(ctx->aux));
     }
     for (size_t i = 0; i < nbins; ++i) buf[i] = (double)h[i];
   } else {
     if (nbins != (size_t)r.p.cam_nbins) return fail(ctx, COLT_EINVAL, "nbins mismatch");
     if (!r.tally.block) { std::memset(buf, 0, sizeof(double) * nbins); return COLT_OK; }
     CU(cudaMemcpyAsync(buf, r.tally.cam_spec + (size_t)camera * r.p.cam_nbins, sizeof(double) * nbins,
-                       cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+                       cudaMemcpyDeviceToHost, ctx->aux));
+    CU(cudaStreamSynchronize(ctx->aux));
   }
   return COLT_OK;
 }
@@ -1256,8 +1358,8 @@ int colt_read_image(colt_ctx* ctx, colt_req req, int camera, double* buf, size_t
   if (n != (size_t)np * np * r.p.cam_nbins) return fail(ctx, COLT_EINVAL, "image size mismatch");
   if (!r.tally.block || !r.tally.cam_image) { std::memset(buf, 0, sizeof(double) * n); return COLT_OK; }
   CU(cudaMemcpyAsync(buf, r.tally.cam_image + r.run.cam[camera].img_off, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                     ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
+                     ctx->aux));
+  CU(cudaStreamSynchronize(ctx->aux));
   return COLT_OK;
 }
 

@@ -21,9 +21,12 @@ constexpr int kMaxCams = 8;
 //   node[v] <  0 : v is leaf -1 - node[v]
 //   nbr[6 i + 2 a + (0: +a face, 1: -a face)] = the node across that face at
 //     the leaf's level or the coarser leaf covering it, packed as
-//     id | level << 27; kNoNbr when the face is on the box boundary.
+//     id | level << 27; when that node is a leaf, id is the leaf's index and
+//     bit 26 (kLeafFlag) is set, so a walk needs no node-table load to find
+//     it; kNoNbr when the face is on the box boundary.
 constexpr uint32_t kNoNbr = 0xFFFFFFFFu;
-constexpr uint32_t kNodeMask = (1u << 27) - 1u;
+constexpr uint32_t kLeafFlag = 1u << 26;
+constexpr uint32_t kNodeMask = (1u << 26) - 1u;
 constexpr int kMaxOctLevel = 24;
 
 // Eq. atau0J, a tau_J = 6.428e4 T_4^(-1/2) (n_HI / cm^-3)^(1/2), in terms of the
@@ -163,6 +166,8 @@ struct LaunchDev {
   unsigned long long* counters = nullptr;    // [kNumLaunchCounters]
   int* error = nullptr;                      // device-side error flag
   unsigned long long* job_max = nullptr;     // [n_jobs] longest history (scatterings), or null
+  int refill_min = 1;                        // a warp refills once this many lanes wait (or all idle)
+  unsigned long long* job_done = nullptr;    // [n_jobs] finished packets, mapped host memory, or null
 };
 
 // launchers (transport.cu)
@@ -173,13 +178,16 @@ struct LaunchDev {
 // blocks_per_sm 0 = as many CTAs as fit.  extras: some job uses diffuse
 // emission or the Jeans core-skipping estimate (their kernel instantiation,
 // register variant 0).
+// warps: warps per CTA, 8 for every variant; the FP32 variant 0 is also built
+// with 4 and 16 (transport_has_warps).
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
-                             int sm_count, cudaStream_t s, bool extras);
+                             int sm_count, cudaStream_t s, bool extras, int warps = 8);
 // true when a job needs the extras instantiation
 inline bool run_needs_extras(const RunDev& r) { return r.source == 1 || r.core_skip == 2; }
 int transport_variants(int precision);
-// resident CTAs per SM of a variant
-int transport_occupancy(int precision, int kind, int variant);
+bool transport_has_warps(int precision, int variant, int warps);
+// resident CTAs per SM of a variant and block size
+int transport_occupancy(int precision, int kind, int variant, int warps = 8);
 // grid preparation (grid.cu)
 cudaError_t launch_atau_nl(const GridDev& g, const float* n_hi, double f_nl, float4* rec_mut, cudaStream_t s);
 // octree grids: lev / ijk are the device copies of the leaves' levels and coordinates

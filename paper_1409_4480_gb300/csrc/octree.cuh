@@ -43,13 +43,19 @@ __device__ __forceinline__ int64_t oct_descend(const GridDev& G, uint32_t v, con
   return -1 - (int64_t)ch;
 }
 
-// Cross the face of leaf `cell` on axis ax towards sgn (the packet lies on
-// that face).  Returns the new leaf, or -1 when the face is the box boundary.
-// ci, *lvl and xi become the new leaf's.
+// The neighbour-table entry of leaf `cell`'s face on axis ax towards sgn.
+__device__ __forceinline__ uint32_t oct_face_entry(const GridDev& G, int64_t cell, int ax, int sgn) {
+  return __ldg(G.nbr + 6 * cell + 2 * ax + (sgn > 0 ? 0 : 1));
+}
+
+// Cross a face whose neighbour-table entry nb the caller has loaded (a walk
+// loads the next face's entry together with the leaf's record, so that the
+// two loads overlap).  The packet lies on that face of the current leaf.
+// Returns the new leaf, or -1 when the face is the box boundary; ci, *lvl and
+// xi become the new leaf's.
 template <typename R>
-__device__ __forceinline__ int64_t oct_cross(const GridDev& G, int64_t cell, int ax, int sgn, const R k[3],
-                                             int ci[3], int* lvl, CellPos<R> xi[3]) {
-  const uint32_t nb = __ldg(G.nbr + 6 * cell + 2 * ax + (sgn > 0 ? 0 : 1));
+__device__ __forceinline__ int64_t oct_cross_entry(const GridDev& G, uint32_t nb, int ax, int sgn, const R k[3],
+                                                   int ci[3], int* lvl, CellPos<R> xi[3]) {
   if (nb == kNoNbr) return -1;
   const int ln = (int)(nb >> 27);
   const int d = *lvl - ln;
@@ -63,7 +69,16 @@ __device__ __forceinline__ int64_t oct_cross(const GridDev& G, int64_t cell, int
     ci[a] = top;
   }
   *lvl = ln;
+  if (nb & kLeafFlag) return (int64_t)(nb & kNodeMask);   // a leaf of that level: no descent
   return oct_descend<R>(G, nb & kNodeMask, k, xi, ci, lvl);
+}
+
+// Cross the face of leaf `cell` on axis ax towards sgn (oct_cross_entry with
+// the entry loaded here).
+template <typename R>
+__device__ __forceinline__ int64_t oct_cross(const GridDev& G, int64_t cell, int ax, int sgn, const R k[3],
+                                             int ci[3], int* lvl, CellPos<R> xi[3]) {
+  return oct_cross_entry<R>(G, oct_face_entry(G, cell, ax, sgn), ax, sgn, k, ci, lvl, xi);
 }
 
 }  // namespace colt

@@ -185,6 +185,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 
   // lane packet state
   bool alive = false, done = false;
+  bool pend_done = false;   // the lane's packet finished this round: count it once its tallies are out
+  int pend_job = 0;
   int jb = 0;
   const Job* J = L.jobs;
   uint64_t pid = 0;
@@ -243,6 +245,8 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       P.t.pk_nscat[pid] = nscat;
       P.t.pk_freq[pid] = sfreq;   // escape frequency; at the cap for max_scatter caps; else 0
     }
+    pend_done = true;
+    pend_job = jb;
     alive = false;
   };
 
@@ -337,7 +341,10 @@ k_transport(const LaunchDev* __restrict__ Lp) {
   for (;;) {
     bool has_peel = false;
     // ---------------------------------------------------------- refill --
-    const unsigned need = __ballot_sync(kFull, !alive && !done);
+    // lanes without a packet take new ones when at least refill_min of them
+    // wait (one atomic serves them all), or when the whole warp is idle
+    const unsigned want = __ballot_sync(kFull, !alive && !done);
+    const unsigned need = (want && (__popc(want) >= L.refill_min || __ballot_sync(kFull, alive) == 0u)) ? want : 0u;
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
@@ -526,9 +533,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       uint32_t visits = 0;
       for (;;) {
         if (++visits > kMaxFlightVisits) { status = 3; break; }
-        const R H = voigt<R>(R(r0.y), x);
-        ktot = R(r0.x) * H + R(r0.z);
-        // distance to the exit face (cm)
+        // distance to the exit face (cm): geometry only, so it comes first
         R tmin = R(3.0e38);
         int ax = 0;
 #pragma unroll
@@ -539,6 +544,11 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             if (d < tmin) { tmin = d; ax = a; }
           }
         }
+        // octree: the exit face's neighbour entry, in flight during the Voigt
+        // evaluation (unused when the packet interacts in this leaf)
+        const uint32_t nbf = kOct ? oct_face_entry(G, c, ax, k[ax] > R(0) ? 1 : -1) : 0u;
+        const R H = voigt<R>(R(r0.y), x);
+        ktot = R(r0.x) * H + R(r0.z);
         if (tau.reached(ktot * tmin)) {
           const R le = m_div(tau.value(), ktot);
 #pragma unroll
@@ -553,7 +563,7 @@ k_transport(const LaunchDev* __restrict__ Lp) {
         if constexpr (kOct) {
           xi[ax].set(sgn > 0 ? R(1) : R(0));
           const int lvl_old = lvl;
-          const int64_t nl = oct_cross<R>(G, c, ax, sgn, k, ci, &lvl, xi);
+          const int64_t nl = oct_cross_entry<R>(G, nbf, ax, sgn, k, ci, &lvl, xi);
           if (nl < 0) {
             escaped = true;
             break;
@@ -746,10 +756,15 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             const R l0 = (s > 0 ? e.xt[ax] : e.xi[ax]) * hax;
             lc[kPeelRays]++;
             lc[kPeelVisits]++;
+            // octree: the event leaf's face entry, loaded before the first
+            // cell's Voigt so that the two overlap
+            uint32_t nbe = kOct ? oct_face_entry(G, e.cell, ax, s) : 0u;
             tau_acc = (e.kHI * voigt<R>(e.a, xc) + e.kd) * l0;
             if constexpr (kOct) {
               // octree: this lane walks the ray leaf by leaf to the cutoff or
-              // the box edge (the next leaf depends on the last one)
+              // the box edge.  The next leaf depends on the last one; each
+              // step loads the leaf's record and its next face entry together,
+              // so one memory latency (not two) separates the steps.
               const float4* __restrict__ rec = G.rec;
               const R tmax = prm<R>(P.tau_max, P.f.tau_max);
               const R h0ax = prm<R>(G.h[ax], G.hf[ax]);
@@ -760,18 +775,17 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #pragma unroll
               for (int a = 0; a < 3; ++a) xj[a].set(e.xi[a]);
               int lv = e.lvl;
-              int64_t cur = e.cell;
               for (uint32_t guard = 0; tau_acc <= tmax && guard < kMaxFlightVisits; ++guard) {
                 xj[ax].set(s > 0 ? R(1) : R(0));
-                const int64_t nx = oct_cross<R>(G, cur, ax, s, kr, cj, &lv, xj);
+                const int64_t nx = oct_cross_entry<R>(G, nbe, ax, s, kr, cj, &lv, xj);
                 if (nx < 0) break;
                 if (nx >= G.n_cells) { atomicExch(L.error, 1); tau_acc = R(3.0e38); break; }
+                nbe = oct_face_entry(G, nx, ax, s);
                 const float4 q0 = __ldg(rec + 2 * nx);
                 const float uq = __ldg(reinterpret_cast<const float*>(rec + 2 * nx + 1) + ax);
                 const R xcell = Vr * R(q0.w) - (s > 0 ? R(uq) : R(-uq));
                 tau_acc += (R(q0.x) * voigt<R>(R(q0.y), xcell) + R(q0.z)) * (h0ax * pow2neg<R>(lv));
                 lc[kPeelVisits]++;
-                cur = nx;
               }
               remaining = 0;
             } else {
@@ -839,6 +853,20 @@ k_transport(const LaunchDev* __restrict__ Lp) {
       }
     }
     __syncwarp();
+    // packets that finished this round (their last peel-off, e.g. at a
+    // scattering cap, tallied just above by some lane of the warp) are counted
+    // to their jobs after a system-scope fence, so that a host which sees a
+    // job's count complete finds its tallies complete.  One lane fences for
+    // the warp (the warp barrier orders every lane's tally writes before it).
+    if (L.job_done) {
+      const unsigned fin = __ballot_sync(kFull, pend_done);
+      if (fin) {
+        if (lane == __ffs(fin) - 1) __threadfence_system();
+        __syncwarp();
+        if (pend_done) atomicAdd_system(L.job_done + pend_job, 1ull);
+      }
+    }
+    pend_done = false;
     COLT_PHASE(2);
 #ifdef COLT_PHASE_CLOCKS
     ph[3] += 1;
@@ -864,15 +892,14 @@ k_transport(const LaunchDev* __restrict__ Lp) {
 #undef COLT_MARK
 }
 
-template <typename R>
+template <typename R, int kWarps>
 constexpr size_t transport_smem() {
-  return (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * 8;
+  return (sizeof(PeelEv<R>) + sizeof(int) + 2 * sizeof(R)) * 32 * kWarps;
 }
 
-template <typename R, bool kOct, int kMinBlocks, bool kX = false>
+template <typename R, bool kOct, int kMinBlocks, bool kX = false, int kWarps = 8>
 static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStream_t s) {
-  constexpr int kWarps = 8;
-  const size_t smem = transport_smem<R>();
+  const size_t smem = transport_smem<R, kWarps>();
   auto kern = k_transport<R, kWarps, kOct, kMinBlocks, kX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -885,21 +912,31 @@ static cudaError_t launch_t(const LaunchDev* L, int bps, int sm_count, cudaStrea
   return cudaGetLastError();
 }
 
-template <typename R, bool kOct, int kMinBlocks>
+template <typename R, bool kOct, int kMinBlocks, int kWarps = 8>
 static int occupancy_t() {
-  constexpr int kWarps = 8;
   auto kern = k_transport<R, kWarps, kOct, kMinBlocks, false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem<R>()) != cudaSuccess)
+  constexpr size_t smem = transport_smem<R, kWarps>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 1;
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, transport_smem<R>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
   return occ < 1 ? 1 : occ;
 }
 
 int transport_variants(int precision) { return precision == 0 ? 1 : 3; }
 
+bool transport_has_warps(int precision, int variant, int warps) {
+  return warps == 8 || (precision == 1 && variant == 0 && (warps == 4 || warps == 16));
+}
+
 cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int variant, int blocks_per_sm,
-                             int sm_count, cudaStream_t s, bool extras) {
+                             int sm_count, cudaStream_t s, bool extras, int warps) {
+  if (!extras && precision == 1 && variant == 0 && warps == 4)
+    return kind == 1 ? launch_t<float, true, 1, false, 4>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<float, false, 1, false, 4>(L, blocks_per_sm, sm_count, s);
+  if (!extras && precision == 1 && variant == 0 && warps == 16)
+    return kind == 1 ? launch_t<float, true, 1, false, 16>(L, blocks_per_sm, sm_count, s)
+                     : launch_t<float, false, 1, false, 16>(L, blocks_per_sm, sm_count, s);
   if (extras) {
     // diffuse emission / Jeans estimate: the compiler's register allocation
     if (precision == 0)
@@ -922,7 +959,11 @@ cudaError_t launch_transport(const LaunchDev* L, int precision, int kind, int va
                    : launch_t<float, false, 1>(L, blocks_per_sm, sm_count, s);
 }
 
-int transport_occupancy(int precision, int kind, int variant) {
+int transport_occupancy(int precision, int kind, int variant, int warps) {
+  if (precision == 1 && variant == 0 && warps == 4)
+    return kind == 1 ? occupancy_t<float, true, 1, 4>() : occupancy_t<float, false, 1, 4>();
+  if (precision == 1 && variant == 0 && warps == 16)
+    return kind == 1 ? occupancy_t<float, true, 1, 16>() : occupancy_t<float, false, 1, 16>();
   if (precision == 0) return kind == 1 ? occupancy_t<double, true, 1>() : occupancy_t<double, false, 1>();
   if (variant == 1) return kind == 1 ? occupancy_t<float, true, 4>() : occupancy_t<float, false, 4>();
   if (variant == 2) return kind == 1 ? occupancy_t<float, true, 3>() : occupancy_t<float, false, 3>();

@@ -152,3 +152,66 @@ def image_blocks_test(xa, xb, min_nonzero=0.75):
         return int(np.count_nonzero(use)), 0.0, 1.0
     z, chi2, p = batch_means_test(xa[:, use], xb[:, use])
     return int(np.count_nonzero(use)), chi2, p
+
+
+def permutation_test(xa, xb, n_perm=20000, seed=12345, chunk=500):
+    """Two-sample permutation test of bin means from equal-size batches.
+
+    xa (B_a, k), xb (B_b, k): the per-packet mean of every bin in each batch;
+    all batches hold the same number of packets, so under the null hypothesis
+    (one distribution) the B_a + B_b batches are exchangeable whatever the
+    shape of that distribution (peel-off weights are heavy-tailed).  The
+    statistic T = sum_bins (mean_a - mean_b)^2 / s^2, with s^2 the variance of
+    the pooled batches (unchanged by relabelling), is compared with its value
+    over random relabellings.  Bins with no spread in the pool are skipped.
+    Returns (bins used, T, p) with p = (1 + #{T_perm >= T}) / (1 + n_perm)."""
+    xa, xb = np.asarray(xa, float), np.asarray(xb, float)
+    pool = np.concatenate([xa, xb], axis=0)
+    s2 = pool.var(axis=0, ddof=1)
+    use = s2 > 0
+    if np.count_nonzero(use) == 0:
+        return 0, 0.0, 1.0
+    pool = pool[:, use] / np.sqrt(s2[use])
+    Ba = xa.shape[0]
+    n = pool.shape[0]
+    tot = pool.sum(axis=0)
+
+    def stat(sa):                      # sa: (..., k) sums over the relabelled sample a
+        return np.sum((sa / Ba - (tot - sa) / (n - Ba)) ** 2, axis=-1)
+    t_obs = float(stat(pool[:Ba].sum(axis=0)))
+    rng = np.random.default_rng(seed)
+    ge = 0
+    done = 0
+    while done < n_perm:
+        m = min(chunk, n_perm - done)
+        idx = np.argsort(rng.random((m, n)), axis=1)[:, :Ba]
+        ge += int(np.count_nonzero(stat(pool[idx].sum(axis=1)) >= t_obs))
+        done += m
+    return int(np.count_nonzero(use)), t_obs, (1.0 + ge) / (1.0 + n_perm)
+
+
+def camera_permutation_test(ga, gb, min_eff=30.0, n_perm=20000):
+    """Camera spectra of two batch sets of equal batch size: ga, gb lists of
+    (cam_spec, cam_spec2, n_packets) per batch.  Bins are merged per camera
+    to min_eff effective contributions on each side (as merge_weighted), and
+    each camera is a permutation test over the merged bins.  Returns per
+    camera (groups, T, p, max_rel) with max_rel the largest relative
+    difference of the two per-packet group means."""
+    out = []
+    n_cam = ga[0][0].shape[0]
+    for c in range(n_cam):
+        Sa = sum(b[0][c] for b in ga)
+        Qa = sum(b[1][c] for b in ga)
+        Sb = sum(b[0][c] for b in gb)
+        Qb = sum(b[1][c] for b in gb)
+        groups = merge_weighted(Sa, Qa, Sb, Qb, min_eff)
+        if len(groups) < 1:
+            out.append(dict(groups=0, T=0.0, p=1.0, max_rel=0.0))
+            continue
+        xa = np.array([[b[0][c][g].sum() / b[2] for g in groups] for b in ga])
+        xb = np.array([[b[0][c][g].sum() / b[2] for g in groups] for b in gb])
+        k, T, p = permutation_test(xa, xb, n_perm)
+        ma, mb = xa.mean(axis=0), xb.mean(axis=0)
+        rel = np.abs(ma - mb) / np.maximum(np.abs(mb), 1e-300)
+        out.append(dict(groups=len(groups), T=T, p=p, max_rel=float(rel.max())))
+    return out

@@ -1,9 +1,6 @@
 """Host-side logic of the benchmark (no GPU): workload definitions, the
-flux-table observables, and the rule that the reported DRAM traffic comes
+flux-table observables, and the rule that the roofline figures come
 only from a capture of the current kernel sources."""
-import hashlib
-import os
-
 import numpy as np
 import pytest
 
@@ -52,18 +49,32 @@ def test_galaxy_models_and_observables():
     assert o["Fr/Fb_z"] > 1e10 and o["f_esc"] == 1.0
 
 
-def test_traffic_only_from_a_capture_of_the_current_kernel(tmp_path, monkeypatch):
-    h = hashlib.sha256()
-    for f in bench.KERNEL_SOURCES:
-        with open(os.path.join(bench.ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    good = tmp_path / "good.md"
-    good.write_text(f"kernel_source_sha256: `{h.hexdigest()}`\ndram_bytes_per_unit: 0.5\n")
-    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(good))
-    assert bench.dram_bytes_per_scattering() == pytest.approx(0.5)
-    stale = tmp_path / "stale.md"
-    stale.write_text("kernel_source_sha256: `" + "0" * 64 + "`\ndram_bytes_per_unit: 0.5\n")
-    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(stale))
-    assert bench.dram_bytes_per_scattering() is None
-    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(tmp_path / "missing.md"))
-    assert bench.dram_bytes_per_scattering() is None
+def test_roofline_only_from_a_capture_of_the_current_kernel(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()
+    (tmp_path / "k_transport_good.md").write_text(
+        f"kernel_source_sha256: `{h}`\nfp32_flop_per_scattering: 600\ndram_bytes_per_scattering: 0.5\n")
+    (tmp_path / "k_transport_stale.md").write_text(
+        "kernel_source_sha256: `" + "0" * 64 + "`\nfp32_flop_per_scattering: 600\ndram_bytes_per_scattering: 0.5\n")
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    u = bench.profile_units("good")
+    assert u["fp32_flop_per_scattering"] == 600 and u["dram_bytes_per_scattering"] == 0.5
+    assert bench.profile_units("stale") is None and bench.profile_units("missing") is None
+    info = {"sm_count": 152}
+    r = bench.roofline(u, scat=1e9, kernel_ms=1000.0, served_rate=2e9, info=info)
+    peak = 152 * 128 * 2 * bench.measured_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak)
+    assert r["achieved"] == pytest.approx(600 * 1e9 / 1.0 / 1e12)        # FP32 operations of the launch / its time
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["traffic"] == pytest.approx(0.5 * 1e9)
+    assert r["frac_served"] == pytest.approx(600 * 2e9 / 1e12 / peak)
+    n = bench.roofline(None, 1e9, 1000.0, 2e9, info)
+    assert n["achieved"] is None and n["traffic"] is None
+
+
+def test_cosmo_step_specs_disjoint_ids():
+    srcs = [((float(i), 0.0, 0.0), 0.0) for i in range(5)]
+    a = bench.cosmo_specs(srcs, [], 256, 100, 0)
+    b = bench.cosmo_specs(srcs, [], 256, 100, 500)
+    ids = [(sp.seed, sp.pid_offset + k) for sp in a + b for k in range(sp.n_packets)]
+    assert len(ids) == len(set(ids)) and len(a) == 5 and all(sp.n_packets == 100 for sp in a)
+    assert [sp.seed for sp in a] == [300, 301, 302, 303, 304]

@@ -80,7 +80,7 @@ def test_non_finite_device_records_raise_the_device_error(colt):
 
 
 def test_cancel_running_and_queued_requests(colt, ctx):
-    g, spec = _long_request(5 << 20)     # more packets than the three serving launches (2^20 each) take
+    g, spec = _long_request(8 << 20)     # more packets than the six serving launches (2^20 each) take
     h = colt.colt_create_grid(ctx, g)
     try:
         rid = colt.colt_submit(ctx, h, spec)

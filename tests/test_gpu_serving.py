@@ -119,6 +119,16 @@ def test_autotune_keeps_results(colt):
         before = colt.colt_run(ctx, h, sp)
         cfg = colt.colt_autotune(ctx, h, sp)
         assert cfg["variant"] in (0, 1, 2) and cfg["blocks_per_sm"] >= 1 and cfg["scatterings_per_s"] > 0
+        assert cfg["warps_per_block"] in (4, 8, 16) and cfg["refill_min"] in (1, 4, 12)
+        # every block size and refill threshold gives the same results
+        for w, m in ((4, 1), (16, 12), (8, 32)):
+            colt.colt_set_launch_config(ctx, colt.COLT_MIXED, colt.COLT_CARTESIAN, 0, 0, w, m)
+            r = colt.colt_run(ctx, h, sp)
+            assert np.array_equal(r["spec"], before["spec"]) and r["n_scat"] == before["n_scat"]
+        with pytest.raises(colt.ColtError):
+            colt.colt_set_launch_config(ctx, colt.COLT_PLAIN, colt.COLT_CARTESIAN, 0, 0, 16, 1)   # FP64: 8 warps only
+        colt.colt_set_launch_config(ctx, colt.COLT_MIXED, colt.COLT_CARTESIAN, cfg["variant"], cfg["blocks_per_sm"],
+                                    cfg["warps_per_block"], cfg["refill_min"])
         after = colt.colt_run(ctx, h, sp)
         rid = colt.colt_submit(ctx, h, sp)
         colt.colt_wait(ctx, rid, timeout_ms=120000)
