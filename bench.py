@@ -742,19 +742,24 @@ def run_serving(args):
     C.colt_finalize(ctx)
 
 
-def launch_count(C, ctx, h=None):
-    """Transport launches issued so far, read through a zero-packet request
-    (it completes at once and launches nothing) on grid h, or on a one-cell
-    grid made for the purpose."""
+def launch_stats(C, ctx, h=None):
+    """(transport launches issued, launches finished and timed, their summed
+    CUDA-event milliseconds) so far, read through a zero-packet request (it
+    completes at once and launches nothing) on grid h, or on a one-cell grid
+    made for the purpose."""
     tmp = None
     if h is None:
         tmp = h = C.colt_create_grid(ctx, S.uniform_box((1, 1, 1), (-1.0,) * 3, (1.0,) * 3, 0.0, 1e4))
     rid = C.colt_submit(ctx, h, S.RunSpec(n_packets=0, seed=0))
-    n = C.colt_poll(ctx, rid)["launches"]
+    st = C.colt_poll(ctx, rid)
     C.colt_release(ctx, rid)
     if tmp is not None:
         C.colt_destroy_grid(ctx, tmp)
-    return n
+    return st["launches"], st["timed_launches"], st["kernel_ms"]
+
+
+def launch_count(C, ctx, h=None):
+    return launch_stats(C, ctx, h)[0]
 
 
 def read_with_images(C, ctx, rid, sp):
@@ -808,11 +813,12 @@ def fp32_peak_tflops(info):
     return info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12, sm_max
 
 
-def roofline(units, scat, kernel_ms, served_rate, info):
-    """`alu` roofline of the transport kernel: achieved = FP32 operations of
-    one launch (the profile's per-scattering count x the launch's executed
-    scatterings) / that launch's CUDA-event time; frac_served the same count
-    at the served scattering rate."""
+def roofline(units, scat, kernel_ms, served_rate, info, launches=1):
+    """`alu` roofline of the transport kernel: achieved = FP32 operations per
+    launch (the profile's per-scattering count x the scatterings of a launch)
+    / the launch's average CUDA-event duration, i.e. the FP32 operations of
+    `launches` launches over their summed device time; frac_served the same
+    count at the served (wall) scattering rate."""
     peak, sm_max = fp32_peak_tflops(info)
     src = f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz (max SM clock, of measured)"
     if not units or units.get("fp32_flop_per_scattering") is None:
@@ -821,11 +827,13 @@ def roofline(units, scat, kernel_ms, served_rate, info):
     f = units["fp32_flop_per_scattering"]
     achieved = f * scat / (kernel_ms * 1e-3) / 1e12
     d = units.get("dram_bytes_per_scattering")
+    n = max(int(launches), 1)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": d * scat if d is not None else None,
-            "traffic_unit": "DRAM bytes per launch (the profile's bytes per scattering x the launch's scatterings)",
+            "traffic": d * scat / n if d is not None else None,
+            "traffic_unit": "DRAM bytes per launch (the profile's bytes per scattering x a launch's scatterings)",
             "flop_per_scattering": f, "frac_served": f * served_rate / 1e12 / peak,
-            "launch": {"scatterings": scat, "kernel_ms": kernel_ms},
+            "launches": {"count": n, "scatterings": scat, "kernel_ms_total": kernel_ms,
+                         "kernel_ms_avg": kernel_ms / n},
             "profile": units["profile"], "peak_source": src}
 
 
@@ -887,7 +895,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                                                  1 << 16, 1 << 40, cap=2000)[0])
     served_burst(C, ctx, stream, [(hw, sp) for s in range(args.warmup) for sp in step_specs(s, cap=10000)])
     C.colt_destroy_grid(ctx, hw)
-    launches0 = launch_count(C, ctx, None)
+    launches0, timed0, kms0 = launch_stats(C, ctx, None)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -921,7 +929,8 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         C.colt_destroy_grid(ctx, h)
         e[3].record(stream)
         torch.cuda.synchronize()
-    launches = launch_count(C, ctx, None) - launches0
+    launches1, timed1, kms1 = launch_stats(C, ctx, None)
+    launches = launches1 - launches0
     ms = e[1].elapsed_time(e[2])
     ms_e2e = e[0].elapsed_time(e[3])
     if world > 1:
@@ -952,7 +961,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                         "image cubes -> colt_destroy_grid"},
         "plain": {"value": plain_scat / (plain_ms * 1e-3), "unit": UNIT, "kernel_ms": plain_ms,
                   "scatterings": plain_scat, "path": "colt_run_batch: one launch of one step's five solves"},
-        "roofline": roofline(units, plain_scat, plain_ms, value, info),
+        "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0),
         "gpu_launches": launches, "clocks": clk.summary(),
         "config": {"workload": label, "sources": ns, "packets_per_source_per_step": B,
                    "cameras": "3 x 512^2 x 256 (+x, +y, +z)",

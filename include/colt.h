@@ -139,12 +139,17 @@ typedef struct {
   int npix;
 } colt_camera;
 
+/* One of several point sources of a solve (colt_run_params.sources). */
+typedef struct {
+  double pos[3];            /* position (cm)                                          */
+  double sigma;             /* Gaussian spread (cm), 0 = point                        */
+  double weight;            /* relative luminosity, >= 0 (not all 0)                  */
+} colt_source;
+
 typedef struct {
   uint64_t n_packets;
   uint64_t seed;            /* Philox key; results depend only on (seed, packet id) */
-  double src_pos[3];        /* point source position (cm); several sources are several
-                               solves on the same grid (batched or served together),
-                               packets in proportion to their luminosities          */
+  double src_pos[3];        /* point source position (cm), when n_sources = 0         */
   double src_sigma;         /* Gaussian spread of the source (cm), 0 = point          */
   int core_skip;            /* COLT_SKIP_* (Sec. 3.2.4); any other nonzero value is
                                rejected                                             */
@@ -176,9 +181,16 @@ typedef struct {
                                COLT_EMIT_NATURAL_THERMAL: x = x_nat + k.u_atom with a
                                Lorentzian x_nat (width a) and a Maxwellian atom velocity
                                of the source cell (Sec. 3.1.1)                      */
-  int source;               /* COLT_SOURCE_POINT (src_pos, src_sigma) or
+  int source;               /* COLT_SOURCE_POINT (src_pos, src_sigma, or sources) or
                                COLT_SOURCE_CELLS (the grid's cell luminosities;
-                               src_pos and src_sigma unused)                        */
+                               src_pos, src_sigma and sources unused)               */
+  int n_sources;            /* 0: the one source src_pos / src_sigma; 1..16: each
+                               packet starts at sources[s] (plus its Gaussian spread)
+                               with probability weight_s / sum of weights, drawn
+                               exactly from integer weights floor(2^(63-b) w_s /
+                               max w), b the least integer with 2^b >= n_sources + 1,
+                               by the 64-bit word of its emission's Philox block 4   */
+  const colt_source* sources; /* host array of n_sources (copied by the call)         */
 } colt_run_params;
 
 /* Outputs of a run.  Counters are always filled; every array pointer may be
@@ -280,6 +292,9 @@ typedef struct {
   uint64_t ctx_launches;    /* transport kernel launches this context has issued */
   int cancelled;            /* 1 after colt_cancel: the tallies cover packets_done
                                packets (those that had started), not packets_total */
+  uint64_t ctx_timed_launches; /* finished transport launches of this context ...     */
+  double ctx_kernel_ms;     /* ... and their summed device time (CUDA events around
+                               each kernel on its own stream)                      */
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double),
                 ("cam_nbins", C.c_int), ("fov_half", C.c_double), ("n_threads", C.c_int),
                 ("pk_status", C.c_void_p), ("pk_nscat", C.c_void_p), ("pk_freq", C.c_void_p),
-                ("pid0", C.c_uint64), ("emission", C.c_int), ("source", C.c_int), ("exact", C.c_int)]
+                ("pid0", C.c_uint64), ("emission", C.c_int), ("source", C.c_int),
+                ("n_sources", C.c_int), ("sources", C.c_void_p), ("exact", C.c_int)]
 
 
 class Result(C.Structure):
@@ -260,6 +261,10 @@ def _params(g, spec, n_threads, per_packet, images, pid0, exact):
     p.max_scatter = int(spec.max_scatter)
     p.emission = int(getattr(spec, "emission", 0) or 0)
     p.source = int(getattr(spec, "source", 0) or 0)
+    srcs = list(getattr(spec, "sources", None) or [])
+    p.n_sources = len(srcs)
+    src_arr = np.array([[*map(float, pos), float(sig), float(w)] for pos, sig, w in srcs], np.float64).reshape(-1)
+    p.sources = _ptr(src_arr) if srcs else None
     p.exact = int(bool(exact))
     p.spec_units = int(spec.spec_units)
     p.T_ref = float(spec.T_ref)
@@ -277,7 +282,7 @@ def _params(g, spec, n_threads, per_packet, images, pid0, exact):
     p.fov_half = float(fov)
     p.n_threads = int(n_threads)
     out = {}
-    keep = [cams]
+    keep = [cams, src_arr]
     if per_packet:
         out["pk_status"] = np.zeros(spec.n_packets, np.int32)
         out["pk_nscat"] = np.zeros(spec.n_packets, np.uint64)

@@ -144,6 +144,12 @@ typedef struct {
   uint64_t  pid0;           /* packets are ids pid0 .. pid0 + n_packets - 1     */
   int       emission;       /* 0 line centre (x = 0), 1 natural + thermal        */
   int       source;         /* 0 point (src_pos, src_sigma), 1 cells by luminosity */
+  int       n_sources;      /* 0: the one source src_pos / src_sigma; else n point
+                               sources, 5 doubles each in `sources` (x, y, z, sigma,
+                               weight); each packet draws its source by weight from
+                               the 64-bit word of event-0 block 4 (integer weights as
+                               for diffuse emission)                                  */
+  const double* sources;
   int       exact;          /* exact-physics mode, for measuring the bias of the
                                approximations: H(a,x) by quadrature instead of
                                H_approx, and u_par at |x| >= 9 by numeric

@@ -227,12 +227,38 @@ static void run_packet(worker* w, uint64_t idx) {
     o_cell_bounds(g, c, clo, chi);
     for (int i = 0; i < 3; ++i) r[i] = clo[i] + B3[i] * (chi[i] - clo[i]);
   } else {
-    if (p->src_sigma > 0.0) {
+    double sigma = p->src_sigma;
+    if (p->n_sources > 0) {
+      /* several point sources, chosen with probability proportional to their
+       * weights: integer weights w_s = floor(2^(63-b) weight_s / max weight),
+       * b the least integer with 2^b >= n + 1; t = floor(word W / 2^64) from
+       * the 64-bit word of event-0 block 4 (words 0 and 1); the source is the
+       * first whose inclusive prefix weight exceeds t */
+      int n = p->n_sources, b = 0;
+      double wmax = 0.0;
+      for (int i = 0; i < n; ++i) if (p->sources[5 * i + 4] > wmax) wmax = p->sources[5 * i + 4];
+      while (b < 63 && ((uint64_t)1 << b) < (uint64_t)n + 1) ++b;
+      uint64_t W = 0;
+      for (int i = 0; i < n; ++i) W += (uint64_t)floor(ldexp(p->sources[5 * i + 4] / wmax, 63 - b));
+      uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), 0u, 4u}, q[4];
+      o_philox4x32_10(ctr, w->key, q);
+      uint64_t word = ((uint64_t)q[1] << 32) | q[0];
+      uint64_t t = (uint64_t)(((unsigned __int128)word * W) >> 64);
+      uint64_t cum = 0;
+      int s = 0;
+      for (; s < n; ++s) {
+        cum += (uint64_t)floor(ldexp(p->sources[5 * s + 4] / wmax, 63 - b));
+        if (cum > t) break;
+      }
+      for (int i = 0; i < 3; ++i) r[i] = p->sources[5 * s + i];
+      sigma = p->sources[5 * s + 3];
+    }
+    if (sigma > 0.0) {
       draw_block(w->key, pid, 0, 1, B1);
       double rho1 = sqrt(-2.0 * log(B1[0])), rho2 = sqrt(-2.0 * log(B1[2]));
-      r[0] += p->src_sigma * rho1 * cos(2.0 * O_PI * B1[1]);
-      r[1] += p->src_sigma * rho1 * sin(2.0 * O_PI * B1[1]);
-      r[2] += p->src_sigma * rho2 * cos(2.0 * O_PI * B1[3]);
+      r[0] += sigma * rho1 * cos(2.0 * O_PI * B1[1]);
+      r[1] += sigma * rho1 * sin(2.0 * O_PI * B1[1]);
+      r[2] += sigma * rho2 * cos(2.0 * O_PI * B1[3]);
     }
     c = o_locate_cell(g, r, k);
   }

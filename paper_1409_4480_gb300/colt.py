@@ -63,7 +63,11 @@ class RunParams(C.Structure):
                 ("cam_units", C.c_int), ("cam_lo", C.c_double), ("cam_hi", C.c_double), ("cam_nbins", C.c_int),
                 ("fov_half", C.c_double), ("precision", C.c_int), ("block_size", C.c_int),
                 ("blocks_per_sm", C.c_int), ("pid_offset", C.c_uint64), ("emission", C.c_int),
-                ("source", C.c_int)]
+                ("source", C.c_int), ("n_sources", C.c_int), ("sources", C.c_void_p)]
+
+
+class Source(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("sigma", C.c_double), ("weight", C.c_double)]
 
 
 class Result(C.Structure):
@@ -79,7 +83,8 @@ class Result(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("done", C.c_int), ("admitted", C.c_int), ("packets_done", C.c_uint64),
                 ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double),
-                ("ctx_launches", C.c_uint64), ("cancelled", C.c_int)]
+                ("ctx_launches", C.c_uint64), ("cancelled", C.c_int), ("ctx_timed_launches", C.c_uint64),
+                ("ctx_kernel_ms", C.c_double)]
 
 
 class LaunchConfig(C.Structure):
@@ -293,7 +298,15 @@ def run_params(spec, images: bool = False):
     p.pid_offset = int(getattr(spec, "pid_offset", 0) or 0)
     p.emission = int(getattr(spec, "emission", 0) or 0)
     p.source = int(getattr(spec, "source", 0) or 0)
-    return p, cams
+    srcs = list(getattr(spec, "sources", None) or [])
+    p.n_sources = len(srcs)
+    arr = (Source * max(1, len(srcs)))()
+    for i, (pos, sig, w) in enumerate(srcs):
+        arr[i].pos = (C.c_double * 3)(*[float(v) for v in pos])
+        arr[i].sigma = float(sig)
+        arr[i].weight = float(w)
+    p.sources = C.cast(arr, C.c_void_p) if srcs else None
+    return p, (cams, arr)
 
 
 def _result_arrays(spec, per_packet, images, grid_npix=None):
@@ -397,7 +410,7 @@ def colt_poll(ctx, req: int) -> dict:
     _check(ctx, lib().colt_poll(ctx, C.c_uint64(req), C.byref(done), C.byref(st)))
     return dict(done=bool(done.value), admitted=bool(st.admitted), packets_done=st.packets_done,
                 packets_total=st.packets_total, latency_ms=st.submit_to_done_ms, launches=st.ctx_launches,
-                cancelled=bool(st.cancelled))
+                cancelled=bool(st.cancelled), timed_launches=st.ctx_timed_launches, kernel_ms=st.ctx_kernel_ms)
 
 
 def colt_wait(ctx, req: int, timeout_ms: float = -1.0):

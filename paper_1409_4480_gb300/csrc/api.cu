@@ -91,6 +91,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t done = nullptr;
+  cudaEvent_t k0 = nullptr, k1 = nullptr;   // around the transport kernel (timing)
+  bool timed = false;                       // k0/k1 hold a launch not yet accounted
   bool in_flight = false;
   std::vector<std::pair<uint64_t, uint64_t>> jobs;  // (request id, packets)
   std::vector<char> credited;                       // job's packets already counted to its request
@@ -119,6 +121,7 @@ struct Req {
   colt_grid grid = 0;
   colt_run_params p{};
   std::vector<colt_camera> cams;
+  std::vector<colt_source> srcs;
   RunDev run;                           // tally pointers filled at admission
   Tally tally;
   int state = kQueued;
@@ -154,6 +157,8 @@ struct colt_ctx {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_alloc = nullptr;
   uint64_t launches = 0;                // transport kernel launches issued
+  uint64_t timed_launches = 0;          // ... of them completed and timed
+  double kernel_ms = 0.0;               // their summed device time (CUDA events on their streams)
   // completion signal of serving launches: a host function enqueued behind
   // each launch bumps done_seq, so colt_wait wakes when ANY slot finishes
   std::mutex cv_mu;
@@ -260,6 +265,8 @@ int ensure_slot(colt_ctx* ctx, int si) {
     sl.own_stream = true;
   }
   CU(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+  CU(cudaEventCreate(&sl.k0));
+  CU(cudaEventCreate(&sl.k1));
   lb.bytes = lb.off_jobs() + sizeof(Job) * kMaxJobs;
   CU(cudaMallocHost(&lb.host, lb.bytes));
   CU(cudaMalloc(&lb.dev, lb.bytes));
@@ -300,8 +307,11 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
   if (blocks_per_sm > 0) {
     CU(cudaMemcpyAsync(lb.dev, lb.host, lb.bytes, cudaMemcpyHostToDevice, sl.stream));
     CU(cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream));
+    CU(cudaEventRecord(sl.k0, sl.stream));
     CU(launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant, blocks_per_sm,
                         ctx->sm_count, sl.stream, extras, warps));
+    CU(cudaEventRecord(sl.k1, sl.stream));
+    sl.timed = true;
     CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
@@ -328,7 +338,12 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     if (ie != cudaSuccess) return cuda_fail(ctx, ie, "cudaGraphInstantiate");
     sl.graph_cfg[gi][gk] = code;
   }
+  // the graph holds the header copy and counter reset before the kernel and
+  // one small copy after it: its time is the kernel's to within those
+  CU(cudaEventRecord(sl.k0, sl.stream));
   CU(cudaGraphLaunch(sl.graph[gi][gk], sl.stream));
+  CU(cudaEventRecord(sl.k1, sl.stream));
+  sl.timed = true;
   return COLT_OK;
 }
 
@@ -601,9 +616,21 @@ void credit_jobs(colt_ctx* ctx, int si, bool all) {
 }
 
 // A slot's launch finished: account its packets to its requests.
+// Add a finished launch's device time to the context's totals.
+void account_launch(colt_ctx* ctx, Slot& sl) {
+  if (!sl.timed) return;
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, sl.k0, sl.k1) == cudaSuccess) {
+    ctx->kernel_ms += ms;
+    ++ctx->timed_launches;
+  }
+  sl.timed = false;
+}
+
 int complete_slot(colt_ctx* ctx, int si) {
   Slot& sl = ctx->slots[si];
   sl.in_flight = false;
+  account_launch(ctx, sl);
   for (size_t j = 0; j < sl.jobs.size(); ++j) {
     auto it = ctx->reqs.find(sl.jobs[j].first);
     if (it != ctx->reqs.end()) learn_cost(ctx, it->second->grid, sl.lb.jmax_h[j]);
@@ -839,6 +866,8 @@ void colt_finalize(colt_ctx* ctx) {
       if (sl.lb.jdone_h) cudaFreeHost(sl.lb.jdone_h);
       if (sl.lb.error) cudaFree(sl.lb.error);
       if (sl.done) cudaEventDestroy(sl.done);
+      if (sl.k0) cudaEventDestroy(sl.k0);
+      if (sl.k1) cudaEventDestroy(sl.k1);
       if (sl.own_stream) cudaStreamDestroy(sl.stream);
     }
     cudaEventDestroy(ctx->ev0);
@@ -1058,6 +1087,7 @@ int colt_run_batch(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_
     if (se != cudaSuccess) { free_all(); return cuda_fail(ctx, se, "transport kernel"); }
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   }
+  if (total > 0) account_launch(ctx, ctx->slots[0]);
   rc = check_device_error(ctx, 0);
   if (total > 0 && !rc)
     for (int q = 0; q < n; ++q) learn_cost(ctx, grids[ord[q]], lb.jmax_h[q]);
@@ -1197,6 +1227,8 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   r->p = *p;
   r->cams.assign(p->cams, p->cams + p->n_cam);
   r->p.cams = r->cams.data();
+  if (p->n_sources > 0) r->srcs.assign(p->sources, p->sources + p->n_sources);
+  r->p.sources = r->srcs.data();
   r->need_bytes = tally_bytes(&r->p, false) + 256;
   size_t grids_bytes = 0;
   for (auto& kv : ctx->grids) grids_bytes += kv.second.bytes;
@@ -1234,6 +1266,8 @@ int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
     st->submit_to_done_ms = r.state == kDone ? r.t_done - r.t_submit : 0.0;
     st->ctx_launches = ctx->launches;
     st->cancelled = r.cancelled ? 1 : 0;
+    st->ctx_timed_launches = ctx->timed_launches;
+    st->ctx_kernel_ms = ctx->kernel_ms;
   }
   return COLT_OK;
 }

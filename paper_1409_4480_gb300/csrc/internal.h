@@ -10,6 +10,7 @@
 namespace colt {
 
 constexpr int kMaxCams = 8;
+constexpr int kMaxSources = 16;
 
 // Per-cell record, two float4 (32 bytes, one DRAM/L2 sector):
 //   r0 = (k_HI = n_HI sigma_0 [1/cm], a, k_dust [1/cm], 1/v_th [s/km])
@@ -96,6 +97,13 @@ struct RunDev {
   Rng rng{0, 0};
   double src[3] = {0, 0, 0};
   double src_sigma = 0;
+  // several point sources: positions, spreads and inclusive prefix sums of
+  // the integer weights (n_src = 0: the one source above)
+  int n_src = 0;
+  double src_pos[kMaxSources][3] = {};
+  double src_sig[kMaxSources] = {};
+  unsigned long long src_cum[kMaxSources] = {};
+  unsigned long long src_total = 0;
   int core_skip = 1, recoil = 1, phase = 0;   // core_skip: COLT_SKIP_*
   int emission = 0;           // 0 line centre, 1 natural + thermal (Sec. 3.1.1)
   int source = 0;             // COLT_SOURCE_POINT / COLT_SOURCE_CELLS

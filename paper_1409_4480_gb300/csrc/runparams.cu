@@ -45,6 +45,21 @@ const char* check_run_params(const colt_run_params* p, bool has_luminosity) {
   if (!(p->tau_esc_max > 0)) return "tau_esc_max must be > 0";
   if (!(p->albedo >= 0 && p->albedo <= 1)) return "albedo must be in [0,1]";
   if (!(p->src_sigma >= 0)) return "src_sigma must be >= 0";
+  if (p->n_sources < 0 || p->n_sources > kMaxSources) return "n_sources must be in [0, 16]";
+  if (p->n_sources > 0) {
+    if (!p->sources) return "sources is NULL";
+    if (p->source != COLT_SOURCE_POINT) return "sources[] needs COLT_SOURCE_POINT";
+    double wmax = 0;
+    for (int i = 0; i < p->n_sources; ++i) {
+      const colt_source& q = p->sources[i];
+      if (!(q.sigma >= 0) || !std::isfinite(q.sigma)) return "source sigma must be >= 0";
+      if (!(q.weight >= 0) || !std::isfinite(q.weight)) return "source weight must be >= 0";
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(q.pos[a])) return "source position must be finite";
+      wmax = std::max(wmax, q.weight);
+    }
+    if (!(wmax > 0)) return "some source weight must be > 0";
+  }
   return nullptr;
 }
 
@@ -55,6 +70,21 @@ RunDev make_run_dev(const double lo[3], const double hi[3], const colt_run_param
   r.rng = Rng{uint32_t(p->seed), uint32_t(p->seed >> 32)};
   for (int a = 0; a < 3; ++a) r.src[a] = p->src_pos[a];
   r.src_sigma = p->src_sigma;
+  if (p->n_sources > 0) {
+    // integer weights floor(2^(63 - b) w / max w), 2^b >= n + 1: they sum below 2^63
+    const int n = p->n_sources;
+    double wmax = 0;
+    for (int i = 0; i < n; ++i) wmax = std::max(wmax, p->sources[i].weight);
+    int b = 0;
+    while (b < 63 && (1ull << b) < (unsigned long long)n + 1) ++b;
+    r.n_src = n;
+    for (int i = 0; i < n; ++i) {
+      for (int a = 0; a < 3; ++a) r.src_pos[i][a] = p->sources[i].pos[a];
+      r.src_sig[i] = p->sources[i].sigma;
+      r.src_total += (unsigned long long)std::floor(std::ldexp(p->sources[i].weight / wmax, 63 - b));
+      r.src_cum[i] = r.src_total;
+    }
+  }
   r.core_skip = p->core_skip;
   r.recoil = p->recoil ? 1 : 0;
   r.phase = p->phase;

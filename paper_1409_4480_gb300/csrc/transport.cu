@@ -390,15 +390,28 @@ k_transport(const LaunchDev* __restrict__ Lp) {
             }
           } else {
             double r[3] = {P.src[0], P.src[1], P.src[2]};
-            if (P.src_sigma > 0.0) {
+            double sig = P.src_sigma;
+            if (P.n_src > 0) {
+              // several sources: the first whose inclusive prefix weight exceeds
+              // t = floor(word W / 2^64), word the 64 bits of event-0 block 4
+              const u4 q4 = P.rng.block(rpid, 0, 4);
+              const unsigned long long t = __umul64hi(((unsigned long long)q4.y << 32) | q4.x, P.src_total);
+              int si = 0;
+              while (si < P.n_src - 1 && !(P.src_cum[si] > t)) ++si;
+              r[0] = P.src_pos[si][0];
+              r[1] = P.src_pos[si][1];
+              r[2] = P.src_pos[si][2];
+              sig = P.src_sig[si];
+            }
+            if (sig > 0.0) {
               U4<double> b1 = uniforms<double>(P.rng, rpid, 0, 1);
               const double rho1 = sqrt(-2.0 * log(b1.v[0])), rho2 = sqrt(-2.0 * log(b1.v[2]));
               double s1, c1, s2, c2;
               sincospi(2.0 * b1.v[1], &s1, &c1);
               sincospi(2.0 * b1.v[3], &s2, &c2);
-              r[0] += P.src_sigma * rho1 * c1;
-              r[1] += P.src_sigma * rho1 * s1;
-              r[2] += P.src_sigma * rho2 * c2;
+              r[0] += sig * rho1 * c1;
+              r[1] += sig * rho1 * s1;
+              r[2] += sig * rho2 * c2;
             }
             if constexpr (kOct) {
               // descend from the root, split planes lo + (2i + 1) h 2^-d

@@ -99,6 +99,7 @@ class RunSpec:
     pid_offset: int = 0             # packets are ids pid_offset .. pid_offset + n_packets - 1
     emission: int = 0               # 0 line centre, 1 natural (Lorentzian) + thermal atom velocity
     source: int = 0                 # 0 point (src_pos, src_sigma), 1 cells by luminosity (Grid.lum)
+    sources: list = dataclasses.field(default_factory=list)   # [(pos, sigma, weight)]: several point sources
 
 
 def sigma0_recipe(T: float) -> float:

@@ -205,3 +205,36 @@ def test_diffuse_natural_emission_mixes_the_cells_voigt_profiles(O):
     m = p_bins * N > 5
     chi2 = np.sum((counts[m] - N * p_bins[m]) ** 2 / (N * p_bins[m]))
     assert stats.chi2.sf(chi2, np.count_nonzero(m) - 1) > 1e-3
+
+
+def test_several_point_sources_in_proportion_to_their_weights(O):
+    # an empty box: every packet leaves unscattered, and its emission peel-off
+    # (weight 1, no attenuation) lands in the pixel of the source it was born
+    # at; the sources' shares of the image follow their weights (binomial),
+    # and a source of weight 0 never emits
+    g = S.uniform_box((4, 4, 4), (-4e18,) * 3, (4e18,) * 3, 1e-30, 1e4)
+    pos = [(-3e18, -3e18, 0.0), (1e18, -3e18, 0.0), (-3e18, 1e18, 0.0), (3e18, 3e18, 0.0)]
+    w = [1.0, 2.0, 5.0, 0.0]
+    N = 40000
+    spec = S.RunSpec(n_packets=N, seed=17, spec_units=1, spec_lo=-50, spec_hi=50, spec_nbins=10,
+                     cameras=S.axis_cameras(8, ("+z",)), cam_units=1, cam_lo=-50, cam_hi=50, cam_nbins=1,
+                     sources=[(p, 0.0, wi) for p, wi in zip(pos, w)])
+    r = O.run(g, spec, images=True)
+    img = r["cam_image"].reshape(8, 8)                      # [v][u]; u = +x, v = +y for the +z camera
+    pix = lambda p: (int((p[1] + 4e18) / 1e18), int((p[0] + 4e18) / 1e18))
+    got = np.array([img[pix(p)] for p in pos])
+    assert got.sum() == pytest.approx(N) and got[3] == 0
+    for k in range(3):
+        f = w[k] / sum(w)
+        assert abs(got[k] - N * f) < 4 * np.sqrt(N * f * (1 - f)), (k, got)
+
+
+def test_one_listed_source_equals_the_single_source(O):
+    g = S.sphere(16, 1e4, 1e5, v_max_kms=50.0, tau_dust=0.5)
+    base = S.RunSpec(n_packets=600, seed=9, src_pos=(2e17, -1e17, 3e17), src_sigma=1e17, albedo=0.32,
+                     spec_units=1, spec_lo=-300, spec_hi=300, spec_nbins=30, max_scatter=50)
+    a = O.run(g, base, per_packet=True)
+    b = O.run(g, S.RunSpec(**{**base.__dict__, "src_pos": (0.0, 0.0, 0.0), "src_sigma": 0.0,
+                              "sources": [((2e17, -1e17, 3e17), 1e17, 3.0)]}), per_packet=True)
+    for k in ("pk_status", "pk_nscat", "pk_freq", "spec"):
+        assert np.array_equal(a[k], b[k])
