@@ -1190,7 +1190,7 @@ def run_profile_case(args):
         h = C.colt_create_grid(ctx, g)
         if name == "cosmo":
             # one source (a few GB on the device: the grid and one solve's image cubes)
-            specs = cosmo_specs(srcs[:1], cams, cnb, 16384, 0)
+            specs = cosmo_specs(srcs[:1], cams, cnb, 65536, 0)
         else:
             pos, sig = srcs[0]
             specs = [S.RunSpec(n_packets=65536, seed=300, src_pos=pos, src_sigma=sig, albedo=0.32, spec_units=1,
