@@ -941,12 +941,6 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         c = torch.tensor([scat, pk], device="cuda", dtype=torch.float64)
         dist.all_reduce(c)
         scat, pk = int(c[0].item()), int(c[1].item())
-    # one plain launch of one step (the dominant kernel's own time, for the roofline)
-    hp = C.colt_create_grid(ctx, g)
-    plain = C.colt_run_batch(ctx, [hp] * ns, step_specs(args.warmup + args.steps), images=True, outputs=False)
-    C.colt_destroy_grid(ctx, hp)
-    plain_scat = sum(r["n_scat"] for r in plain)
-    plain_ms = plain[0]["kernel_ms"]
     value = scat / (ms * 1e-3)
     units = profile_units("cosmo")
     return {
@@ -959,8 +953,6 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                 "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit "
                         "of every step -> colt_wait -> colt_read_result with escape spectra, camera spectra and "
                         "image cubes -> colt_destroy_grid"},
-        "plain": {"value": plain_scat / (plain_ms * 1e-3), "unit": UNIT, "kernel_ms": plain_ms,
-                  "scatterings": plain_scat, "path": "colt_run_batch: one launch of one step's five solves"},
         "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0),
         "gpu_launches": launches, "clocks": clk.summary(),
         "config": {"workload": label, "sources": ns, "packets_per_source_per_step": B,
@@ -1156,7 +1148,7 @@ def run_suite(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "photons_per_s": head["photons_per_s"], "served_latency_ms": head["latency"], "config": head["config"],
             "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "e2e": head["e2e"],
-            "plain": head["plain"], "clocks": head["clocks"],
+            "clocks": head["clocks"],
             "counts": {"scatterings": head["scat"], "packets": head["packets"]}}
     if rank == 0 and world == 1:
         wl = {}
@@ -1223,8 +1215,8 @@ def main():
     ap.add_argument("--packets-per-case", type=int, default=None,
                     help="single-workload modes: packets per solve per step (default: 125000 for the sphere suite "
                          "and --single-case; 4096 halo / halo_diffuse / galaxies, 2048 cosmo, 20000 tslab)")
-    ap.add_argument("--cosmo-packets", type=int, default=256, help="suite headline: packets per source per step")
-    ap.add_argument("--halo-packets", type=int, default=4096, help="suite: halo packets per step")
+    ap.add_argument("--cosmo-packets", type=int, default=1024, help="suite headline: packets per source per step")
+    ap.add_argument("--halo-packets", type=int, default=8192, help="suite: halo packets per step")
     ap.add_argument("--halo-steps", type=int, default=8, help="suite: halo steps")
     ap.add_argument("--sphere-steps", type=int, default=6, help="suite: sphere-suite steps")
     ap.add_argument("--fp64-packets", type=int, default=100000, help="suite: packets of the plain FP64 solve")

@@ -258,8 +258,7 @@ typedef struct {
  * refill threshold (1, 4, 12), one solve per configuration.  The fastest is
  * kept for params->precision and the grid's kind (every later launch of that
  * pair with blocks_per_sm = 0 uses it, served launches included) and reported
- * in *out (may be NULL).  Blocking; about eleven solves for FP32, four for
- * FP64. */
+ * in *out (may be NULL).  Blocking; ten solves for FP32, four for FP64. */
 int colt_autotune(colt_ctx* ctx, colt_grid grid, const colt_run_params* params, colt_launch_config* out);
 
 /* Set the launch configuration used for `precision` (COLT_PLAIN / COLT_MIXED)
@@ -304,9 +303,10 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
  * colt_poll and colt_wait. */
 int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st);
 /* Block until req is done or timeout_ms (< 0: no limit) elapses
- * (COLT_ETIMEOUT).  While waiting it sleeps until any in-flight launch
- * finishes and then refills the free slot, so other requests keep the GPU
- * busy; it re-polls at least every 20 ms. */
+ * (COLT_ETIMEOUT; the request keeps running).  While waiting it sleeps until
+ * any in-flight launch finishes and then refills the free slot, so other
+ * requests keep the GPU busy; it re-polls every millisecond, so a request
+ * whose own packets finish inside a running launch is seen done promptly. */
 int colt_wait(colt_ctx* ctx, colt_req req, double timeout_ms);
 /* camera = -1: the angle-averaged escape spectrum (as doubles); else the
  * camera's peel-off spectrum.  nbins must match the request's bin count. */

@@ -15,5 +15,9 @@ int main(void) {
   printf("off_run_emission %zu\n", offsetof(colt_run_params, emission));
   printf("off_run_source %zu\n", offsetof(colt_run_params, source));
   printf("off_result_pk_freq %zu\n", offsetof(colt_result, pk_freq));
+  printf("colt_source %zu\n", sizeof(colt_source));
+  printf("off_run_sources %zu\n", offsetof(colt_run_params, sources));
+  printf("off_stats_kernel_ms %zu\n", offsetof(colt_stats, ctx_kernel_ms));
+  printf("off_launch_refill_min %zu\n", offsetof(colt_launch_config, refill_min));
   return 0;
 }

@@ -60,6 +60,10 @@ def test_binding_struct_layout_matches_header():
     assert sizes["off_run_emission"] == colt.RunParams.emission.offset
     assert sizes["off_run_source"] == colt.RunParams.source.offset
     assert sizes["off_result_pk_freq"] == colt.Result.pk_freq.offset
+    assert sizes["colt_source"] == ctypes.sizeof(colt.Source)
+    assert sizes["off_run_sources"] == colt.RunParams.sources.offset
+    assert sizes["off_stats_kernel_ms"] == colt.Stats.ctx_kernel_ms.offset
+    assert sizes["off_launch_refill_min"] == colt.LaunchConfig.refill_min.offset
 
 
 def test_no_cpu_fallback_in_product_path():
