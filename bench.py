@@ -10,9 +10,9 @@ cosmo     the synthetic cosmological box (1 Mpc^3 comoving at z = 10,
           512^2 pixels x 256 bins over +-1000 km/s, mixed precision.  A step is
           one solve per source of --cosmo-packets packets (disjoint packet ids
           per step and rank).  The K timed steps are submitted together to the
-          serving scheduler, as a user submits a job of many steps: its
-          persistent launches overlap, so one step's longest histories run
-          beside the other steps' work.  value = scatterings/s (executed,
+          serving scheduler (colt_submit_many), as a user submits a job of
+          many steps: they share persistent launches, so one step's longest
+          histories run beside the other steps' work.  value = scatterings/s (executed,
           core-skipped ones not counted) over the device-timed region (CUDA
           events on the library's stream, grid resident); photons/s and served
           p50/p99 beside it.  The same pass gives e2e: the grid built from host
@@ -846,7 +846,7 @@ def served_burst(C, ctx, stream, reqs, read=None):
     torch.cuda.synchronize()
     ev0.record(stream)
     t0 = time.perf_counter()
-    ids = [(C.colt_submit(ctx, h, sp, images=read is not None), sp) for h, sp in reqs]
+    ids = list(zip(C.colt_submit_many(ctx, reqs, images=read is not None), [sp for _, sp in reqs]))
     for rid, _ in ids:
         C.colt_wait(ctx, rid, -1.0)
     ev1.record(stream)
@@ -910,7 +910,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         torch.cuda.synchronize()
         e[1].record(stream)
         reqs = [(h, sp) for s in range(args.warmup, args.warmup + args.steps) for sp in step_specs(s)]
-        ids = [(C.colt_submit(ctx, hh, sp), sp) for hh, sp in reqs]
+        ids = list(zip(C.colt_submit_many(ctx, reqs), [sp for _, sp in reqs]))
         for rid, _ in ids:
             C.colt_wait(ctx, rid, -1.0)
         e[2].record(stream)
@@ -950,7 +950,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         "e2e": {"value": scat / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
                 "d2h_bytes_per_step": int(d2h // args.steps), "ms_per_step": ms_e2e / args.steps,
                 "steps": args.steps,
-                "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit "
+                "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit_many "
                         "of every step -> colt_wait -> colt_read_result with escape spectra, camera spectra and "
                         "image cubes -> colt_destroy_grid"},
         "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0),
@@ -961,7 +961,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                            f"(refined on density; the workload description names levels 7-14, the density "
                            f"criterion of this generator stops at 12)",
                    "precision": "mixed (FP32 transport, FP32-pair position and tau, FP64 escape and tallies)",
-                   "launch": "served: the K steps submitted together, persistent launches in flight",
+                   "launch": "served: the K steps submitted together (colt_submit_many), persistent launches in flight",
                    "launch_config": dict(tuned, source="colt_autotune on one source, 65536 packets capped at "
                                                        "2000 scatterings"),
                    "warmup": "W steps with histories capped at 1e4 scatterings",

@@ -297,6 +297,16 @@ typedef struct {
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);
+/* Submit n requests at once (grids[i], params[i]) -> out[i] (the serving API
+ * has no counterpart in the paper).  Every request is checked first and none
+ * is queued if one fails (the error of the first that fails); then all are
+ * queued in order and the scheduler takes one step, so a batch fills shared
+ * launches together instead of the first ones each taking a launch slot of
+ * their own (colt_submit schedules after every request).  Admission,
+ * completion and results are those of colt_submit of the same requests in the
+ * same order.  COLT_EAGAIN when the queue cannot hold all n. */
+int colt_submit_many(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
+                     colt_req* out);
 /* Drives the scheduler one step (collects finished launches, admits queued
  * requests, refills free launch slots) and reports the request's state;
  * never blocks on the device.  The scheduler advances only inside colt_submit,

@@ -28,7 +28,7 @@ COLT_SKIP_OFF, COLT_SKIP_CELL_NL, COLT_SKIP_JEANS = 0, 1, 2
 COLT_SOURCE_POINT, COLT_SOURCE_CELLS = 0, 1
 
 EXPORTS = ["colt_init", "colt_finalize", "colt_last_error", "colt_device_info", "colt_create_grid",
-           "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_poll",
+           "colt_destroy_grid", "colt_read_cells", "colt_run", "colt_run_batch", "colt_solve", "colt_submit", "colt_submit_many", "colt_poll",
            "colt_wait", "colt_read_spectrum", "colt_read_image", "colt_read_result", "colt_release", "colt_voigt", "colt_scatter",
            "colt_run_noalloc", "colt_autotune", "colt_set_cell_luminosity", "colt_cancel",
            "colt_set_launch_config"]
@@ -131,6 +131,7 @@ def lib():
             "colt_run_batch": (I, [P, I, P, P, P]),
             "colt_solve": (I, [P, P, P, P]),
             "colt_submit": (I, [P, U64, P, C.POINTER(U64)]),
+            "colt_submit_many": (I, [P, I, P, P, P]),
             "colt_poll": (I, [P, U64, C.POINTER(I), P]),
             "colt_wait": (I, [P, U64, D]),
             "colt_read_spectrum": (I, [P, U64, I, P, SZ]),
@@ -402,6 +403,18 @@ def colt_submit(ctx, grid: int, spec, images: bool = True) -> int:
     h = C.c_uint64()
     _check(ctx, lib().colt_submit(ctx, C.c_uint64(grid), C.byref(p), C.byref(h)))
     return h.value
+
+
+def colt_submit_many(ctx, reqs, images: bool = True) -> list:
+    """Queue several solves at once, reqs = [(grid, spec), ...]: all are
+    checked before any is queued, and they are scheduled together."""
+    n = len(reqs)
+    made = [run_params(spec, images) for _, spec in reqs]   # keeps each camera/source array alive
+    ps = (RunParams * max(n, 1))(*[m[0] for m in made])
+    gs = (C.c_uint64 * max(n, 1))(*[g for g, _ in reqs])
+    hs = (C.c_uint64 * max(n, 1))()
+    _check(ctx, lib().colt_submit_many(ctx, C.c_int(n), gs, ps, hs))
+    return [hs[i] for i in range(n)]
 
 
 def colt_poll(ctx, req: int) -> dict:

@@ -37,6 +37,7 @@ namespace {
 constexpr int kMaxJobs = 256;                  // solves per persistent launch
 constexpr int kSlots = 6;                      // launches in flight (serving)
 constexpr uint64_t kStepPackets = 1ull << 20;  // packet budget of one serving launch
+constexpr size_t kMaxQueued = 4096;             // requests waiting for admission
 constexpr int kWorkWords = 8;                  // work counter + launch counters (+ phase clocks)
 constexpr int kMaxPassed = 4;                  // launches a ready request may be passed over
 
@@ -1212,15 +1213,24 @@ int colt_solve(colt_ctx* ctx, const colt_grid_desc* desc, const colt_run_params*
   return rc;
 }
 
-int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out) {
-  if (!ctx || !out) return COLT_EINVAL;
-  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-  cudaSetDevice(ctx->device);
+// A request that colt_submit would queue (the grid exists, the parameters are
+// valid, the request fits the memory budget alone); its tally bytes in *need.
+static int check_request(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, size_t* need) {
+  if (!p) return COLT_EINVAL;
   auto it = ctx->grids.find(grid);
   if (it == ctx->grids.end()) return fail(ctx, COLT_ENOTFOUND, "unknown grid");
   int rc = validate_params(ctx, p, it->second);
   if (rc) return rc;
-  if (ctx->queue.size() >= 4096) return fail(ctx, COLT_EAGAIN, "request queue full");
+  *need = tally_bytes(p, false) + 256;
+  size_t grids_bytes = 0;
+  for (auto& kv : ctx->grids) grids_bytes += kv.second.bytes;
+  if (grids_bytes + *need > ctx->budget)
+    return fail(ctx, COLT_ENOMEM, "request can never fit in the memory budget");
+  return COLT_OK;
+}
+
+// Queue a checked request (no scheduling step); returns its handle.
+static colt_req enqueue_request(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, size_t need) {
   auto r = std::make_unique<Req>();
   r->id = ctx->next_handle++;
   r->grid = grid;
@@ -1229,12 +1239,8 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   r->p.cams = r->cams.data();
   if (p->n_sources > 0) r->srcs.assign(p->sources, p->sources + p->n_sources);
   r->p.sources = r->srcs.data();
-  r->need_bytes = tally_bytes(&r->p, false) + 256;
-  size_t grids_bytes = 0;
-  for (auto& kv : ctx->grids) grids_bytes += kv.second.bytes;
-  if (grids_bytes + r->need_bytes > ctx->budget)
-    return fail(ctx, COLT_ENOMEM, "request can never fit in the memory budget");
-  r->run = make_run(it->second, &r->p);
+  r->need_bytes = need;
+  r->run = make_run(ctx->grids.at(grid), &r->p);
   r->target = r->p.n_packets;
   r->t_submit = now_ms();
   if (r->p.n_packets == 0) {
@@ -1243,8 +1249,37 @@ int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_re
   } else {
     ctx->queue.push_back(r->id);
   }
-  *out = r->id;
-  ctx->reqs[r->id] = std::move(r);
+  const colt_req id = r->id;
+  ctx->reqs[id] = std::move(r);
+  return id;
+}
+
+int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out) {
+  if (!ctx || !out) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  size_t need = 0;
+  int rc = check_request(ctx, grid, p, &need);
+  if (rc) return rc;
+  if (ctx->queue.size() >= kMaxQueued) return fail(ctx, COLT_EAGAIN, "request queue full");
+  *out = enqueue_request(ctx, grid, p, need);
+  return serve_pump(ctx);
+}
+
+int colt_submit_many(colt_ctx* ctx, int n, const colt_grid* grids, const colt_run_params* params,
+                     colt_req* out) {
+  if (!ctx || n < 0 || (n > 0 && (!grids || !params || !out))) return COLT_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  // every request is checked before any is queued: all or none
+  std::vector<size_t> need(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = check_request(ctx, grids[i], params + i, &need[i]);
+    if (rc) return rc;
+  }
+  if (ctx->queue.size() + (size_t)n > kMaxQueued) return fail(ctx, COLT_EAGAIN, "request queue full");
+  for (int i = 0; i < n; ++i) out[i] = enqueue_request(ctx, grids[i], params + i, need[i]);
+  // one scheduling step for the whole batch: the requests share launches
   return serve_pump(ctx);
 }
 

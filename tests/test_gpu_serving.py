@@ -68,6 +68,53 @@ def test_batched_equals_alone(colt):
         colt.colt_finalize(ctx)
 
 
+def test_submit_many_shares_one_launch_and_equals_alone(colt):
+    # a batch submitted together is scheduled together: the six requests of
+    # the mix (83 700 packets, one precision, Cartesian grids) go into one
+    # launch, where colt_submit would start the first ones in launch slots of
+    # their own; each result still equals the request's solve alone
+    ctx = colt.colt_init(0)
+    try:
+        grids, reqs = _mix()
+        hs = [colt.colt_create_grid(ctx, g) for g in grids]
+        alone = [colt.colt_run(ctx, hs[gi], sp, images=bool(sp.cameras)) for gi, sp in reqs]
+        z = colt.colt_submit(ctx, hs[0], S.RunSpec(n_packets=0, seed=0))     # done at once, launches nothing
+        launches0 = colt.colt_poll(ctx, z)["launches"]
+        colt.colt_release(ctx, z)
+        ids = colt.colt_submit_many(ctx, [(hs[gi], sp) for gi, sp in reqs])
+        assert len(ids) == len(reqs) and ids == sorted(ids)
+        for rid in ids:
+            colt.colt_wait(ctx, rid, timeout_ms=120000)
+        assert colt.colt_poll(ctx, ids[0])["launches"] == launches0 + 1
+        for rid, (gi, sp), ref in zip(ids, reqs, alone):
+            st = colt.colt_poll(ctx, rid)
+            assert st["done"] and st["packets_done"] == sp.n_packets
+            got = colt.colt_read_result(ctx, rid, sp)
+            assert np.array_equal(got["spec"], ref["spec"])
+            for key in ("n_emitted", "n_escaped", "n_absorbed", "n_capped", "n_scat", "n_scat_hi"):
+                assert got[key] == ref[key], key
+            if sp.cameras:
+                assert np.allclose(got["cam_spec"], ref["cam_spec"], rtol=1e-9, atol=1e-300)
+                img = colt.colt_read_image(ctx, rid, 0, 8, sp.cam_nbins)
+                assert np.allclose(img.ravel(), ref["cam_image"][: img.size], rtol=1e-9, atol=1e-300)
+            colt.colt_release(ctx, rid)
+        # all or none: a batch with an unknown grid queues nothing
+        z1 = colt.colt_submit(ctx, hs[0], S.RunSpec(n_packets=0, seed=0))
+        with pytest.raises(colt.ColtError) as e:
+            colt.colt_submit_many(ctx, [(hs[0], reqs[0][1]), (hs[-1] + 1000, reqs[0][1])])
+        assert e.value.code == colt.COLT_ENOTFOUND
+        z2 = colt.colt_submit(ctx, hs[0], S.RunSpec(n_packets=0, seed=0))
+        assert z2 == z1 + 1
+        assert colt.colt_poll(ctx, z2)["launches"] == launches0 + 1
+        for q in (z1, z2):
+            colt.colt_release(ctx, q)
+        assert colt.colt_submit_many(ctx, []) == []
+        for h in hs:
+            colt.colt_destroy_grid(ctx, h)
+    finally:
+        colt.colt_finalize(ctx)
+
+
 def test_admission_by_memory(colt):
     g = S.sphere(16, 1e4, 1e4)
     grid_bytes = g.n_cells * 32
