@@ -837,10 +837,12 @@ def roofline(units, scat, kernel_ms, served_rate, info, launches=1):
             "profile": units["profile"], "peak_source": src}
 
 
-def served_burst(C, ctx, stream, reqs, read=None):
+def served_burst(C, ctx, stream, reqs, read=None, stats=None):
     """Submit every (grid, spec) at once and wait for all: (device ms between
     CUDA events on the library's stream around submit..done, wall s, results
-    of colt_read_result (or read(rid, spec)), per-request latency ms)."""
+    of colt_read_result (or read(rid, spec)), per-request latency ms).  With
+    a dict `stats`, its "longest_history" is set to the most scatterings of
+    one packet over all the requests."""
     import torch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -853,12 +855,16 @@ def served_burst(C, ctx, stream, reqs, read=None):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     out, lat = [], []
+    longest = 0
     for rid, sp in ids:
         st = C.colt_poll(ctx, rid)
         lat.append(st["latency_ms"])
+        longest = max(longest, st["longest_history"])
         r = read(rid, sp) if read else C.colt_read_result(ctx, rid, S.RunSpec(**{**sp.__dict__, "cameras": []}))
         out.append(r)
         C.colt_release(ctx, rid)
+    if stats is not None:
+        stats["longest_history"] = longest
     return ev0.elapsed_time(ev1), wall, out, lat
 
 
@@ -917,9 +923,11 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         torch.cuda.synchronize()
         scat = pk = 0
         lat = []
+        longest = 0
         for rid, sp in ids:
             st = C.colt_poll(ctx, rid)
             lat.append(st["latency_ms"])
+            longest = max(longest, st["longest_history"])
             r = read_with_images(C, ctx, rid, sp)
             d2h += sum(v.nbytes for v in r.values() if isinstance(v, np.ndarray))
             scat += r["n_scat"]
@@ -935,9 +943,9 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
     ms_e2e = e[0].elapsed_time(e[3])
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms, ms_e2e], device="cuda")
+        t = torch.tensor([ms, ms_e2e, float(longest)], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0].item()), float(t[1].item())
+        ms, ms_e2e, longest = float(t[0].item()), float(t[1].item()), int(t[2].item())
         c = torch.tensor([scat, pk], device="cuda", dtype=torch.float64)
         dist.all_reduce(c)
         scat, pk = int(c[0].item()), int(c[1].item())
@@ -945,6 +953,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
     units = profile_units("cosmo")
     return {
         "value": value, "photons_per_s": pk / (ms * 1e-3), "ms": ms, "scat": scat, "packets": pk,
+        "longest_history": longest,
         "latency": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n_requests": len(lat),
                     "arrivals": "burst: the K steps' solves submitted together"},
         "e2e": {"value": scat / (ms_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
@@ -1032,13 +1041,15 @@ def leg_halo(C, ctx, stream, args, info):
             sp.max_scatter = cap
         return sp
     served_burst(C, ctx, stream, [(h, spec(0, cap=10000))])
+    tail = {}
     with ClockSampler(0) as clk:
-        ms, wall, res, lat = served_burst(C, ctx, stream, [(h, spec(s)) for s in range(1, 1 + args.halo_steps)])
+        ms, wall, res, lat = served_burst(C, ctx, stream, [(h, spec(s)) for s in range(1, 1 + args.halo_steps)],
+                                          stats=tail)
     C.colt_destroy_grid(ctx, h)
     scat = sum(r["n_scat"] for r in res)
     pk = sum(r["n_emitted"] for r in res)
     return {"value": scat / (ms * 1e-3), "unit": UNIT, "photons_per_s": pk / (ms * 1e-3), "steps": args.halo_steps,
-            "ms_per_step": ms / args.halo_steps,
+            "ms_per_step": ms / args.halo_steps, "longest_history_scatterings": tail["longest_history"],
             "served_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "n_requests": len(lat),
                                   "arrivals": "burst"},
             "clocks": clk.summary(),
@@ -1149,7 +1160,8 @@ def run_suite(args):
             "photons_per_s": head["photons_per_s"], "served_latency_ms": head["latency"], "config": head["config"],
             "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "e2e": head["e2e"],
             "clocks": head["clocks"],
-            "counts": {"scatterings": head["scat"], "packets": head["packets"]}}
+            "counts": {"scatterings": head["scat"], "packets": head["packets"],
+                       "longest_history_scatterings": head["longest_history"]}}
     if rank == 0 and world == 1:
         wl = {}
         if not args.no_secondary:

@@ -294,6 +294,9 @@ typedef struct {
   uint64_t ctx_timed_launches; /* finished transport launches of this context ...     */
   double ctx_kernel_ms;     /* ... and their summed device time (CUDA events around
                                each kernel on its own stream)                      */
+  uint64_t longest_history; /* most scatterings of one packet of the request, over
+                               the launches of it that have ended (a request can be
+                               done before its last launch ends)                   */
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);

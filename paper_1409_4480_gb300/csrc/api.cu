@@ -133,6 +133,7 @@ struct Req {
   bool cancelled = false;
   double t_submit = 0, t_done = 0;
   size_t need_bytes = 0;
+  uint64_t longest = 0;                 // most scatterings of one packet, over its ended launches
 };
 
 }  // namespace
@@ -634,7 +635,9 @@ int complete_slot(colt_ctx* ctx, int si) {
   account_launch(ctx, sl);
   for (size_t j = 0; j < sl.jobs.size(); ++j) {
     auto it = ctx->reqs.find(sl.jobs[j].first);
-    if (it != ctx->reqs.end()) learn_cost(ctx, it->second->grid, sl.lb.jmax_h[j]);
+    if (it == ctx->reqs.end()) continue;
+    learn_cost(ctx, it->second->grid, sl.lb.jmax_h[j]);
+    it->second->longest = std::max<uint64_t>(it->second->longest, sl.lb.jmax_h[j]);
   }
   credit_jobs(ctx, si, true);
   sl.jobs.clear();
@@ -1303,6 +1306,7 @@ int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
     st->cancelled = r.cancelled ? 1 : 0;
     st->ctx_timed_launches = ctx->timed_launches;
     st->ctx_kernel_ms = ctx->kernel_ms;
+    st->longest_history = r.longest;
   }
   return COLT_OK;
 }

@@ -18,6 +18,7 @@ int main(void) {
   printf("colt_source %zu\n", sizeof(colt_source));
   printf("off_run_sources %zu\n", offsetof(colt_run_params, sources));
   printf("off_stats_kernel_ms %zu\n", offsetof(colt_stats, ctx_kernel_ms));
+  printf("off_stats_longest %zu\n", offsetof(colt_stats, longest_history));
   printf("off_launch_refill_min %zu\n", offsetof(colt_launch_config, refill_min));
   return 0;
 }

@@ -4,6 +4,8 @@ equals its result alone (colt_run with the same grid and parameters):
 integer tallies bitwise, peel-off sums up to FP64 summation order.  Memory
 admission queues what does not fit and rejects what never can."""
 
+import time
+
 import numpy as np
 import pytest
 
@@ -86,9 +88,16 @@ def test_submit_many_shares_one_launch_and_equals_alone(colt):
         for rid in ids:
             colt.colt_wait(ctx, rid, timeout_ms=120000)
         assert colt.colt_poll(ctx, ids[0])["launches"] == launches0 + 1
+        # the longest history is known once the launch has ended (a request
+        # can be done before that): poll until it is, then it lies between
+        # the mean scatterings per packet and the request's total
+        deadline = time.time() + 60.0
+        while colt.colt_poll(ctx, ids[0])["longest_history"] == 0 and time.time() < deadline:
+            time.sleep(0.01)
         for rid, (gi, sp), ref in zip(ids, reqs, alone):
             st = colt.colt_poll(ctx, rid)
             assert st["done"] and st["packets_done"] == sp.n_packets
+            assert ref["n_scat"] / sp.n_packets <= st["longest_history"] <= ref["n_scat"]
             got = colt.colt_read_result(ctx, rid, sp)
             assert np.array_equal(got["spec"], ref["spec"])
             for key in ("n_emitted", "n_escaped", "n_absorbed", "n_capped", "n_scat", "n_scat_hi"):
