@@ -39,7 +39,8 @@ serving   256 requests (spheres or slabs on 64^3, tau0, T, v_max, dust and
 --workload W      one workload alone (sphere128, halo, halo_diffuse, cosmo,
                   serving, tslab, galaxies), for profiling
 --single-case I   one blocking solve of sphere-suite case I (profiling driver)
---profile-case W  one short capped solve of workload W (ncu capture driver)
+--profile-case W  one short capped solve of workload W (ncu capture driver);
+          --profile-no-cameras: the same solves without cameras
 """
 import argparse
 import json
@@ -744,7 +745,8 @@ def run_serving(args):
 
 def launch_stats(C, ctx, h=None):
     """(transport launches issued, launches finished and timed, their summed
-    CUDA-event milliseconds) so far, read through a zero-packet request (it
+    CUDA-event milliseconds, their flight cell visits, their peel-off cell
+    visits) so far, read through a zero-packet request (it
     completes at once and launches nothing) on grid h, or on a one-cell grid
     made for the purpose."""
     tmp = None
@@ -755,7 +757,7 @@ def launch_stats(C, ctx, h=None):
     C.colt_release(ctx, rid)
     if tmp is not None:
         C.colt_destroy_grid(ctx, tmp)
-    return st["launches"], st["timed_launches"], st["kernel_ms"]
+    return st["launches"], st["timed_launches"], st["kernel_ms"], st["cell_visits"], st["peel_visits"]
 
 
 def launch_count(C, ctx, h=None):
@@ -804,6 +806,21 @@ def profile_units(name):
     for key in ("fp32_flop_per_scattering", "dram_bytes_per_scattering"):
         m = re.search(key + r": ([0-9.eE+-]+)", text)
         out[key] = float(m.group(1)) if m else None
+    # the captured launch's work: "<n> scatterings, <n> flight cell visits, <n> peel-off visits"
+    m = re.search(r"(\d+) scatterings, (\d+) flight cell visits, (\d+) peel-off visits", text)
+    if m:
+        s, c, p = (float(v) for v in m.groups())
+        out["visits_per_scattering"] = {"cell": c / s, "peel": p / s}
+    # the same solves without cameras: the per-scattering work with no peel-off
+    try:
+        t0 = open(os.path.join(PROFILES, f"k_transport_{name}_nocam.md")).read()
+    except OSError:
+        t0 = ""
+    m0 = re.search(r"kernel_source_sha256: `([0-9a-f]+)`", t0)
+    m1 = re.search(r"fp32_flop_per_scattering_no_cameras: ([0-9.eE+-]+)", t0)
+    if m0 and m1 and m0.group(1) == kernel_source_hash():
+        out["fp32_flop_per_scattering_no_cameras"] = float(m1.group(1))
+        out["profile_no_cameras"] = os.path.relpath(os.path.join(PROFILES, f"k_transport_{name}_nocam.md"), ROOT)
     return out
 
 
@@ -813,28 +830,45 @@ def fp32_peak_tflops(info):
     return info["sm_count"] * 128 * 2 * sm_max * 1e6 / 1e12, sm_max
 
 
-def roofline(units, scat, kernel_ms, served_rate, info, launches=1):
+def roofline(units, scat, kernel_ms, served_rate, info, launches=1, mix=None):
     """`alu` roofline of the transport kernel: achieved = FP32 operations per
-    launch (the profile's per-scattering count x the scatterings of a launch)
-    / the launch's average CUDA-event duration, i.e. the FP32 operations of
+    launch (a per-scattering count x the scatterings of a launch) / the
+    launch's average CUDA-event duration, i.e. the FP32 operations of
     `launches` launches over their summed device time; frac_served the same
-    count at the served (wall) scattering rate."""
+    count at the served (wall) scattering rate.  The per-scattering count is
+    the capture's, for the capture's work mix; with `mix` (flight cell and
+    peel-off visits per scattering of the timed region) and a capture of the
+    same solves without cameras (F0), it is scaled to the timed region's
+    peel-off work: F0 + (F - F0) x (peel visits per scattering here / in the
+    capture), the peel-off part of the capture taken per visit."""
     peak, sm_max = fp32_peak_tflops(info)
     src = f"{info['sm_count']} SMs x 128 FP32 lanes x 2 x {sm_max:g} MHz (max SM clock, of measured)"
     if not units or units.get("fp32_flop_per_scattering") is None:
         return {"bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "peak_source": src, "note": "no current ncu summary for this kernel"}
-    f = units["fp32_flop_per_scattering"]
+    f_capture = units["fp32_flop_per_scattering"]
+    f0 = units.get("fp32_flop_per_scattering_no_cameras")
+    pv = (units.get("visits_per_scattering") or {}).get("peel")
+    model = "the capture's FP32 operations per scattering (its work mix)"
+    f = f_capture
+    if mix is not None and f0 is not None and pv:
+        f = f0 + (f_capture - f0) * mix["peel"] / pv
+        model = ("F0 + (F - F0) x peel visits per scattering (timed region / capture): F0 from the capture "
+                 "without cameras, F from the capture with them")
     achieved = f * scat / (kernel_ms * 1e-3) / 1e12
     d = units.get("dram_bytes_per_scattering")
     n = max(int(launches), 1)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": d * scat / n if d is not None else None,
-            "traffic_unit": "DRAM bytes per launch (the profile's bytes per scattering x a launch's scatterings)",
-            "flop_per_scattering": f, "frac_served": f * served_rate / 1e12 / peak,
+            "traffic_unit": "DRAM bytes per launch (the capture's bytes per scattering, at the capture's work mix, "
+                            "x a launch's scatterings)",
+            "flop_per_scattering": f, "flop_model": model, "flop_per_scattering_capture": f_capture,
+            "flop_per_scattering_no_cameras": f0, "frac_served": f * served_rate / 1e12 / peak,
             "launches": {"count": n, "scatterings": scat, "kernel_ms_total": kernel_ms,
                          "kernel_ms_avg": kernel_ms / n},
-            "profile": units["profile"], "peak_source": src}
+            "profile": units["profile"], "peak_source": src,
+            **({"visits_per_scattering": {"timed_region": mix, "profile": units.get("visits_per_scattering")}}
+               if mix is not None else {})}
 
 
 def served_burst(C, ctx, stream, reqs, read=None, stats=None):
@@ -901,7 +935,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                                                  1 << 16, 1 << 40, cap=2000)[0])
     served_burst(C, ctx, stream, [(hw, sp) for s in range(args.warmup) for sp in step_specs(s, cap=10000)])
     C.colt_destroy_grid(ctx, hw)
-    launches0, timed0, kms0 = launch_stats(C, ctx, None)
+    launches0, timed0, kms0, cv0, pv0 = launch_stats(C, ctx, None)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -937,7 +971,9 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         C.colt_destroy_grid(ctx, h)
         e[3].record(stream)
         torch.cuda.synchronize()
-    launches1, timed1, kms1 = launch_stats(C, ctx, None)
+    launches1, timed1, kms1, cv1, pv1 = launch_stats(C, ctx, None)
+    # this rank's work mix in the timed region, beside the captured launch's
+    mix = {"cell": (cv1 - cv0) / max(scat, 1), "peel": (pv1 - pv0) / max(scat, 1)}
     launches = launches1 - launches0
     ms = e[1].elapsed_time(e[2])
     ms_e2e = e[0].elapsed_time(e[3])
@@ -962,7 +998,7 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                 "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit_many "
                         "of every step -> colt_wait -> colt_read_result with escape spectra, camera spectra and "
                         "image cubes -> colt_destroy_grid"},
-        "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0),
+        "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0, mix=mix),
         "gpu_launches": launches, "clocks": clk.summary(),
         "config": {"workload": label, "sources": ns, "packets_per_source_per_step": B,
                    "cameras": "3 x 512^2 x 256 (+x, +y, +z)",
@@ -1019,7 +1055,9 @@ def leg_sphere(C, ctx, stream, args, info):
             "plain_fp64": {"value": p64["n_scat"] / (p64["kernel_ms"] * 1e-3), "unit": UNIT,
                            "kernel_ms": p64["kernel_ms"], "packets": args.fp64_packets,
                            "path": "colt_run, precision PLAIN: one solve (tau0 = 1e5, static) per launch"},
-            "roofline": roofline(units, plain_scat, plain_ms, value, info),
+            "roofline": roofline(units, plain_scat, plain_ms, value, info,
+                                 mix={"cell": plain[0]["n_cell_visits"] / max(plain_scat, 1),
+                                      "peel": plain[0]["n_peel_visits"] / max(plain_scat, 1)}),
             "clocks": clk.summary(),
             "config": {"workload": WORKLOAD, "packets_per_case_per_step": B,
                        "cameras": "6 x 128^2 x 200", "precision": "mixed (served, plain); FP64 (plain_fp64)",
@@ -1203,11 +1241,14 @@ def run_profile_case(args):
         hs = [h] * len(specs)
     for sp in specs:
         sp.max_scatter = 2000
+        if args.profile_no_cameras:
+            sp.cameras = []     # the same histories (peel-off draws no random numbers), no peel-off work
     r = C.colt_run_batch(ctx, hs, specs, images=True, outputs=False)
     print(json.dumps({"workload": name, "launches": 1, "kernel_ms": r[0]["kernel_ms"],
                       "scatterings": sum(x["n_scat"] for x in r), "packets": sum(x["n_emitted"] for x in r),
                       "cell_visits": r[0]["n_cell_visits"], "peel_visits": r[0]["n_peel_visits"],
                       "peel_rays": r[0]["n_peel_rays"], "max_scatter": 2000,
+                      "cameras": 0 if args.profile_no_cameras else len(specs[0].cameras),
                       "kernel_source_sha256": kernel_source_hash()}), flush=True)
     C.colt_finalize(ctx)
 
@@ -1236,6 +1277,8 @@ def main():
     ap.add_argument("--ref-packets", type=int, default=16)
     ap.add_argument("--single-case", type=int, default=-1)
     ap.add_argument("--profile-case", default=None, choices=["cosmo", "sphere128", "halo"])
+    ap.add_argument("--profile-no-cameras", action="store_true",
+                    help="with --profile-case: the same solves without cameras (no peel-off work)")
     ap.add_argument("--max-scatter", type=int, default=0)
     ap.add_argument("--no-images", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

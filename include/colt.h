@@ -297,6 +297,8 @@ typedef struct {
   uint64_t longest_history; /* most scatterings of one packet of the request, over
                                the launches of it that have ended (a request can be
                                done before its last launch ends)                   */
+  uint64_t ctx_cell_visits; /* flight cell visits and peel-off cell visits of the  */
+  uint64_t ctx_peel_visits; /* context's finished, timed launches                  */
 } colt_stats;
 
 int colt_submit(colt_ctx* ctx, colt_grid grid, const colt_run_params* p, colt_req* out);

@@ -84,7 +84,8 @@ class Stats(C.Structure):
     _fields_ = [("done", C.c_int), ("admitted", C.c_int), ("packets_done", C.c_uint64),
                 ("packets_total", C.c_uint64), ("submit_to_done_ms", C.c_double),
                 ("ctx_launches", C.c_uint64), ("cancelled", C.c_int), ("ctx_timed_launches", C.c_uint64),
-                ("ctx_kernel_ms", C.c_double), ("longest_history", C.c_uint64)]
+                ("ctx_kernel_ms", C.c_double), ("longest_history", C.c_uint64),
+                ("ctx_cell_visits", C.c_uint64), ("ctx_peel_visits", C.c_uint64)]
 
 
 class LaunchConfig(C.Structure):
@@ -424,7 +425,8 @@ def colt_poll(ctx, req: int) -> dict:
     return dict(done=bool(done.value), admitted=bool(st.admitted), packets_done=st.packets_done,
                 packets_total=st.packets_total, latency_ms=st.submit_to_done_ms, launches=st.ctx_launches,
                 cancelled=bool(st.cancelled), timed_launches=st.ctx_timed_launches, kernel_ms=st.ctx_kernel_ms,
-                longest_history=st.longest_history)
+                longest_history=st.longest_history, cell_visits=st.ctx_cell_visits,
+                peel_visits=st.ctx_peel_visits)
 
 
 def colt_wait(ctx, req: int, timeout_ms: float = -1.0):

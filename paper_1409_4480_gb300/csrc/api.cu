@@ -76,7 +76,8 @@ struct LaunchBuf {
   unsigned char* dev = nullptr;
   size_t bytes = 0;
   unsigned long long* work = nullptr;   // device: next counter + launch counters, then job_max
-  unsigned long long* jmax_h = nullptr; // pinned copy of job_max after the launch
+  unsigned long long* work_h = nullptr; // pinned copy of work after the launch ...
+  unsigned long long* jmax_h = nullptr; // ... and its job_max part
   unsigned long long* jdone_h = nullptr; // pinned, mapped: packets of each job finished (written by the kernel)
   unsigned long long* jdone_d = nullptr; // its device address
   int* error = nullptr;
@@ -161,6 +162,8 @@ struct colt_ctx {
   uint64_t launches = 0;                // transport kernel launches issued
   uint64_t timed_launches = 0;          // ... of them completed and timed
   double kernel_ms = 0.0;               // their summed device time (CUDA events on their streams)
+  uint64_t cell_visits = 0;             // ... and their flight cell and peel-off visits
+  uint64_t peel_visits = 0;
   // completion signal of serving launches: a host function enqueued behind
   // each launch bumps done_seq, so colt_wait wakes when ANY slot finishes
   std::mutex cv_mu;
@@ -273,7 +276,9 @@ int ensure_slot(colt_ctx* ctx, int si) {
   CU(cudaMallocHost(&lb.host, lb.bytes));
   CU(cudaMalloc(&lb.dev, lb.bytes));
   CU(cudaMalloc(&lb.work, sizeof(unsigned long long) * (kWorkWords + kMaxJobs)));
-  CU(cudaMallocHost(&lb.jmax_h, sizeof(unsigned long long) * kMaxJobs));
+  CU(cudaMallocHost(&lb.work_h, sizeof(unsigned long long) * (kWorkWords + kMaxJobs)));
+  std::memset(lb.work_h, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs));
+  lb.jmax_h = lb.work_h + kWorkWords;
   CU(cudaHostAlloc(&lb.jdone_h, sizeof(unsigned long long) * kMaxJobs, cudaHostAllocMapped));
   std::memset(lb.jdone_h, 0, sizeof(unsigned long long) * kMaxJobs);
   CU(cudaMalloc(&lb.error, sizeof(int)));
@@ -314,7 +319,7 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
                         ctx->sm_count, sl.stream, extras, warps));
     CU(cudaEventRecord(sl.k1, sl.stream));
     sl.timed = true;
-    CU(cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
+    CU(cudaMemcpyAsync(lb.work_h, lb.work, sizeof(unsigned long long) * (kWorkWords + kMaxJobs),
                        cudaMemcpyDeviceToHost, sl.stream));
     return COLT_OK;
   }
@@ -330,7 +335,7 @@ int enqueue_launch(colt_ctx* ctx, int si, int precision, int kind, int blocks_pe
     cudaMemsetAsync(lb.work, 0, sizeof(unsigned long long) * (kWorkWords + kMaxJobs), sl.stream);
     cudaError_t le = launch_transport(reinterpret_cast<const LaunchDev*>(lb.dev), precision, kind, cfg.variant,
                                       cfg.blocks_per_sm, ctx->sm_count, sl.stream, extras, warps);
-    cudaMemcpyAsync(lb.jmax_h, lb.work + kWorkWords, sizeof(unsigned long long) * kMaxJobs,
+    cudaMemcpyAsync(lb.work_h, lb.work, sizeof(unsigned long long) * (kWorkWords + kMaxJobs),
                     cudaMemcpyDeviceToHost, sl.stream);
     cudaError_t ce = cudaStreamEndCapture(sl.stream, &g);
     if (le != cudaSuccess) return cuda_fail(ctx, le, "transport launch (capture)");
@@ -617,8 +622,8 @@ void credit_jobs(colt_ctx* ctx, int si, bool all) {
   }
 }
 
-// A slot's launch finished: account its packets to its requests.
-// Add a finished launch's device time to the context's totals.
+// Add a finished launch's device time and its cell and peel-off visits (the
+// launch counters, copied back after the kernel) to the context's totals.
 void account_launch(colt_ctx* ctx, Slot& sl) {
   if (!sl.timed) return;
   float ms = 0;
@@ -626,6 +631,8 @@ void account_launch(colt_ctx* ctx, Slot& sl) {
     ctx->kernel_ms += ms;
     ++ctx->timed_launches;
   }
+  ctx->cell_visits += sl.lb.work_h[1 + kCellVisits];
+  ctx->peel_visits += sl.lb.work_h[1 + kPeelVisits];
   sl.timed = false;
 }
 
@@ -866,7 +873,7 @@ void colt_finalize(colt_ctx* ctx) {
       if (sl.lb.host) cudaFreeHost(sl.lb.host);
       if (sl.lb.dev) cudaFree(sl.lb.dev);
       if (sl.lb.work) cudaFree(sl.lb.work);
-      if (sl.lb.jmax_h) cudaFreeHost(sl.lb.jmax_h);
+      if (sl.lb.work_h) cudaFreeHost(sl.lb.work_h);
       if (sl.lb.jdone_h) cudaFreeHost(sl.lb.jdone_h);
       if (sl.lb.error) cudaFree(sl.lb.error);
       if (sl.done) cudaEventDestroy(sl.done);
@@ -1307,6 +1314,8 @@ int colt_poll(colt_ctx* ctx, colt_req req, int* done, colt_stats* st) {
     st->ctx_timed_launches = ctx->timed_launches;
     st->ctx_kernel_ms = ctx->kernel_ms;
     st->longest_history = r.longest;
+    st->ctx_cell_visits = ctx->cell_visits;
+    st->ctx_peel_visits = ctx->peel_visits;
   }
   return COLT_OK;
 }

@@ -19,6 +19,7 @@ int main(void) {
   printf("off_run_sources %zu\n", offsetof(colt_run_params, sources));
   printf("off_stats_kernel_ms %zu\n", offsetof(colt_stats, ctx_kernel_ms));
   printf("off_stats_longest %zu\n", offsetof(colt_stats, longest_history));
+  printf("off_stats_peel_visits %zu\n", offsetof(colt_stats, ctx_peel_visits));
   printf("off_launch_refill_min %zu\n", offsetof(colt_launch_config, refill_min));
   return 0;
 }

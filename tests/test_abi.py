@@ -64,6 +64,7 @@ def test_binding_struct_layout_matches_header():
     assert sizes["off_run_sources"] == colt.RunParams.sources.offset
     assert sizes["off_stats_kernel_ms"] == colt.Stats.ctx_kernel_ms.offset
     assert sizes["off_stats_longest"] == colt.Stats.longest_history.offset
+    assert sizes["off_stats_peel_visits"] == colt.Stats.ctx_peel_visits.offset
     assert sizes["off_launch_refill_min"] == colt.LaunchConfig.refill_min.offset
 
 

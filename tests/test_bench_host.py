@@ -71,6 +71,34 @@ def test_roofline_only_from_a_capture_of_the_current_kernel(tmp_path, monkeypatc
     assert n["achieved"] is None and n["traffic"] is None
 
 
+def test_roofline_scales_the_capture_to_the_timed_work_mix(tmp_path, monkeypatch):
+    # a capture with cameras (600 FP32 operations per scattering at 20 peel-off
+    # visits per scattering) and the same solves without them (200): the
+    # per-scattering count follows the timed region's peel-off visits
+    h = bench.kernel_source_hash()
+    (tmp_path / "k_transport_w.md").write_text(
+        f"kernel_source_sha256: `{h}`\nfp32_flop_per_scattering: 600\ndram_bytes_per_scattering: 0.5\n"
+        "Launch: 1000 scatterings, 1100 flight cell visits, 20000 peel-off visits (900 rays)\n")
+    (tmp_path / "k_transport_w_nocam.md").write_text(
+        f"kernel_source_sha256: `{h}`\nfp32_flop_per_scattering_no_cameras: 200\n")
+    (tmp_path / "k_transport_v.md").write_text((tmp_path / "k_transport_w.md").read_text())
+    (tmp_path / "k_transport_v_nocam.md").write_text(
+        "kernel_source_sha256: `" + "0" * 64 + "`\nfp32_flop_per_scattering_no_cameras: 200\n")
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    u = bench.profile_units("w")
+    assert u["visits_per_scattering"] == {"cell": 1.1, "peel": 20.0}
+    assert u["fp32_flop_per_scattering_no_cameras"] == 200
+    info = {"sm_count": 152}
+    def f(units, peel):
+        return bench.roofline(units, 1e9, 1000.0, 2e9, info, mix={"cell": 1.0, "peel": peel})["flop_per_scattering"]
+    assert f(u, 20.0) == pytest.approx(600)      # the capture's own mix: its count
+    assert f(u, 0.0) == pytest.approx(200)       # no peel-off: the count without cameras
+    assert f(u, 5.0) == pytest.approx(300)       # a quarter of the capture's peel-off visits
+    assert bench.roofline(u, 1e9, 1000.0, 2e9, info)["flop_per_scattering"] == 600   # no mix given
+    v = bench.profile_units("v")                 # a stale capture without cameras is not used
+    assert "fp32_flop_per_scattering_no_cameras" not in v and f(v, 5.0) == pytest.approx(600)
+
+
 def test_cosmo_step_specs_disjoint_ids():
     srcs = [((float(i), 0.0, 0.0), 0.0) for i in range(5)]
     a = bench.cosmo_specs(srcs, [], 256, 100, 0)

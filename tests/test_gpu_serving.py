@@ -81,7 +81,8 @@ def test_submit_many_shares_one_launch_and_equals_alone(colt):
         hs = [colt.colt_create_grid(ctx, g) for g in grids]
         alone = [colt.colt_run(ctx, hs[gi], sp, images=bool(sp.cameras)) for gi, sp in reqs]
         z = colt.colt_submit(ctx, hs[0], S.RunSpec(n_packets=0, seed=0))     # done at once, launches nothing
-        launches0 = colt.colt_poll(ctx, z)["launches"]
+        st0 = colt.colt_poll(ctx, z)
+        launches0 = st0["launches"]
         colt.colt_release(ctx, z)
         ids = colt.colt_submit_many(ctx, [(hs[gi], sp) for gi, sp in reqs])
         assert len(ids) == len(reqs) and ids == sorted(ids)
@@ -94,6 +95,12 @@ def test_submit_many_shares_one_launch_and_equals_alone(colt):
         deadline = time.time() + 60.0
         while colt.colt_poll(ctx, ids[0])["longest_history"] == 0 and time.time() < deadline:
             time.sleep(0.01)
+        # the context's visit totals grew by the launch's: flight visits are
+        # those of the same packets alone, peel-off visits nearly so
+        st1 = colt.colt_poll(ctx, ids[0])
+        assert st1["cell_visits"] - st0["cell_visits"] == sum(r["n_cell_visits"] for r in alone)
+        pv = sum(r["n_peel_visits"] for r in alone)
+        assert pv > 0 and abs(st1["peel_visits"] - st0["peel_visits"] - pv) <= 1e-3 * pv
         for rid, (gi, sp), ref in zip(ids, reqs, alone):
             st = colt.colt_poll(ctx, rid)
             assert st["done"] and st["packets_done"] == sp.n_packets
