@@ -972,7 +972,9 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
         e[3].record(stream)
         torch.cuda.synchronize()
     launches1, timed1, kms1, cv1, pv1 = launch_stats(C, ctx, None)
-    # this rank's work mix in the timed region, beside the captured launch's
+    # this rank's work mix in the timed region, beside the captured launch's;
+    # the roofline is this rank's launches over their own time
+    scat_rank = scat
     mix = {"cell": (cv1 - cv0) / max(scat, 1), "peel": (pv1 - pv0) / max(scat, 1)}
     launches = launches1 - launches0
     ms = e[1].elapsed_time(e[2])
@@ -998,7 +1000,8 @@ def leg_cosmo(C, ctx, stream, args, info, world, rank):
                 "path": "colt_create_grid from host fields (once, bytes spread over the steps) -> colt_submit_many "
                         "of every step -> colt_wait -> colt_read_result with escape spectra, camera spectra and "
                         "image cubes -> colt_destroy_grid"},
-        "roofline": roofline(units, scat, kms1 - kms0, value, info, launches=timed1 - timed0, mix=mix),
+        "roofline": roofline(units, scat_rank, kms1 - kms0, value / max(world, 1), info, launches=timed1 - timed0,
+                             mix=mix),
         "gpu_launches": launches, "clocks": clk.summary(),
         "config": {"workload": label, "sources": ns, "packets_per_source_per_step": B,
                    "cameras": "3 x 512^2 x 256 (+x, +y, +z)",
